@@ -1,0 +1,354 @@
+/*
+ * CPU oracle: a plain, single-threaded CHP stabilizer simulator over unpacked
+ * bit rows (one uint8_t per tableau bit).
+ *
+ * TEST INFRASTRUCTURE ONLY. It exists to check the CUDA path; only tests, the
+ * smoke check and the benchmark's CPU-baseline leg load it. It shares no code,
+ * header or table with the CUDA library, and it is written for clarity, not
+ * speed.
+ *
+ * What it computes (paper: arXiv 2603.14641):
+ *   - Extended tableau of Sec. 2.5, Eq. 7: rows 0..n-1 are destabilizers
+ *     D_1..D_n, rows n..2n-1 stabilizers S_1..S_n; each row holds x bits,
+ *     z bits and a sign bit r (generator = (-1)^r * P, P encoded per qubit
+ *     by (x,z): (0,0)=I, (1,0)=X, (1,1)=Y, (0,1)=Z, Sec. 2.4).
+ *   - Gates H, P(=S), CX by the column update rules of Sec. 2.4, Eq. 4,
+ *     applied to every row. The rest of the 11-gate set of Sec. 6 is built
+ *     from those rules (X/Y/Z flip the sign of anticommuting rows; S^dag =
+ *     S^3; CZ = H_t CX H_t; CY = S_t CX S_t^dag; SWAP = 3 CX;
+ *     ISWAP = CZ, SWAP, S_a, S_b in circuit order).
+ *   - Z-measurement by the CHP algorithm of Sec. 2.5: pivot = smallest
+ *     stabilizer with x_pq = 1; rowsum of the pivot into every other row
+ *     with x_iq = 1; D_p <- S_p; S_p <- (-1)^m Z_q with m a fresh coin; in the
+ *     deterministic case (-1)^m Z_q = product of S_i over destabilizers D_i
+ *     that anticommute with Z_q, accumulated in a scratch row.
+ *   - rowsum(h, i) of Aaronson & Gottesman (cited in Sec. 2.5): the phase is
+ *     2 r_h + 2 r_i + sum_j g(x_ij, z_ij, x_hj, z_hj) mod 4, where g is the
+ *     exponent of i in the single-qubit product sigma(x_ij,z_ij) *
+ *     sigma(x_hj,z_hj).
+ *   - Pauli-frame sampling of Sec. 5 (Alg. 9) with a reference record
+ *     (the frames carry flips relative to that record).
+ *
+ * Readings of the paper where it is silent or garbled (listed in the design
+ * notes): the rowsum goes into every row i != p (both halves) with x_iq = 1,
+ * skipping the paired destabilizer p-n that is overwritten right after;
+ * destabilizer signs follow the same update rules; the coin is a keyed
+ * Philox4x64-10 bit.
+ *
+ * Keyed randomness: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+ * written here from its published definition:
+ *   coin(seed, shot, m)      = bit 0 of word 0 of Philox(ctr=(m, shot, 0, 0),
+ *                                                     key=(seed, 0x51A7E))
+ *   frame_word(seed, e, q, j) = word (j & 3) of Philox(ctr=(e, q, j >> 2, 1),
+ *                                                     key=(seed, 0xF4A3E))
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon et al. 2011)                                   */
+/* ------------------------------------------------------------------ */
+
+static void mul128(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo) {
+  /* 64x64 -> 128 product from four 32x32 partial products */
+  uint64_t a0 = a & 0xffffffffu, a1 = a >> 32, b0 = b & 0xffffffffu, b1 = b >> 32;
+  uint64_t p00 = a0 * b0, p01 = a0 * b1, p10 = a1 * b0, p11 = a1 * b1;
+  uint64_t mid = (p00 >> 32) + (p01 & 0xffffffffu) + (p10 & 0xffffffffu);
+  *lo = (mid << 32) | (p00 & 0xffffffffu);
+  *hi = p11 + (p01 >> 32) + (p10 >> 32) + (mid >> 32);
+}
+
+void oracle_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
+  uint64_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint64_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t hi0, lo0, hi1, lo1;
+    mul128(0xD2E7470EE14C6C93ull, c0, &hi0, &lo0);
+    mul128(0xCA5A826395121157ull, c2, &hi1, &lo1);
+    uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B97F4A7C15ull; /* Weyl key schedule */
+    k1 += 0xBB67AE8584CAA73Bull;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+int oracle_coin(uint64_t seed, uint64_t shot, uint64_t m) {
+  uint64_t ctr[4] = {m, shot, 0, 0}, key[2] = {seed, 0x51A7Eull}, out[4];
+  oracle_philox4x64_10(ctr, key, out);
+  return (int)(out[0] & 1u);
+}
+
+uint64_t oracle_frame_word(uint64_t seed, uint64_t e, uint64_t q, uint64_t j) {
+  uint64_t ctr[4] = {e, q, j >> 2, 1}, key[2] = {seed, 0xF4A3Eull}, out[4];
+  oracle_philox4x64_10(ctr, key, out);
+  return out[j & 3];
+}
+
+/* ------------------------------------------------------------------ */
+/* Tableau                                                              */
+/* ------------------------------------------------------------------ */
+
+enum { G_I, G_X, G_Y, G_Z, G_H, G_S, G_SDG, G_CX, G_CY, G_CZ, G_SWAP, G_ISWAP };
+
+typedef struct {
+  int n;
+  uint8_t *x; /* (2n+1) rows of n bits; row 2n is the scratch row */
+  uint8_t *z;
+  uint8_t *r; /* 2n+1 sign bits */
+  long odd_phase_count; /* rowsums whose phase was odd (must stay 0) */
+  long det_check_fail;  /* deterministic products that were not +-Z_q */
+  int last_kind;        /* 1 = last measurement was probabilistic, 0 = deterministic */
+} chp_t;
+
+#define XB(t, i, j) ((t)->x[(size_t)(i) * (size_t)(t)->n + (size_t)(j)])
+#define ZB(t, i, j) ((t)->z[(size_t)(i) * (size_t)(t)->n + (size_t)(j)])
+
+void oracle_reset(chp_t *t, const uint8_t *initstate) {
+  int n = t->n;
+  memset(t->x, 0, (size_t)(2 * n + 1) * n);
+  memset(t->z, 0, (size_t)(2 * n + 1) * n);
+  memset(t->r, 0, (size_t)(2 * n + 1));
+  for (int i = 0; i < n; ++i) {
+    XB(t, i, i) = 1;      /* D_i = X_i */
+    ZB(t, n + i, i) = 1;  /* S_i = Z_i */
+    if (initstate && initstate[i]) { t->r[i] = 1; t->r[n + i] = 1; }
+  }
+  t->odd_phase_count = 0;
+  t->det_check_fail = 0;
+  t->last_kind = -1;
+}
+
+chp_t *oracle_new(int n) {
+  chp_t *t = (chp_t *)calloc(1, sizeof(chp_t));
+  if (!t) return NULL;
+  t->n = n;
+  size_t cells = (size_t)(2 * n + 1) * (size_t)(n > 0 ? n : 1);
+  t->x = (uint8_t *)calloc(cells, 1);
+  t->z = (uint8_t *)calloc(cells, 1);
+  t->r = (uint8_t *)calloc((size_t)(2 * n + 1), 1);
+  if (!t->x || !t->z || !t->r) { free(t->x); free(t->z); free(t->r); free(t); return NULL; }
+  oracle_reset(t, NULL);
+  return t;
+}
+
+void oracle_free(chp_t *t) {
+  if (!t) return;
+  free(t->x); free(t->z); free(t->r); free(t);
+}
+
+int oracle_n(const chp_t *t) { return t->n; }
+long oracle_odd_phase_count(const chp_t *t) { return t->odd_phase_count; }
+long oracle_det_check_fail(const chp_t *t) { return t->det_check_fail; }
+int oracle_last_kind(const chp_t *t) { return t->last_kind; }
+
+/* Copy out / in the 2n rows: x, z are 2n*n bytes (row-major), r is 2n bytes. */
+void oracle_get(const chp_t *t, uint8_t *x, uint8_t *z, uint8_t *r) {
+  size_t cells = (size_t)(2 * t->n) * t->n;
+  memcpy(x, t->x, cells); memcpy(z, t->z, cells); memcpy(r, t->r, (size_t)(2 * t->n));
+}
+void oracle_set(chp_t *t, const uint8_t *x, const uint8_t *z, const uint8_t *r) {
+  size_t cells = (size_t)(2 * t->n) * t->n;
+  memcpy(t->x, x, cells); memcpy(t->z, z, cells); memcpy(t->r, r, (size_t)(2 * t->n));
+}
+
+/* --- Sec. 2.4, Eq. 4: the three base rules, applied to every row ------- */
+
+static void rule_h(chp_t *t, int q) {
+  for (int i = 0; i < 2 * t->n; ++i) {
+    uint8_t x = XB(t, i, q), z = ZB(t, i, q);
+    t->r[i] ^= (uint8_t)(x & z);
+    XB(t, i, q) = z;
+    ZB(t, i, q) = x;
+  }
+}
+
+static void rule_p(chp_t *t, int q) {
+  for (int i = 0; i < 2 * t->n; ++i) {
+    uint8_t x = XB(t, i, q), z = ZB(t, i, q);
+    t->r[i] ^= (uint8_t)(x & z);
+    ZB(t, i, q) = (uint8_t)(z ^ x);
+  }
+}
+
+static void rule_cx(chp_t *t, int c, int tq) {
+  for (int i = 0; i < 2 * t->n; ++i) {
+    uint8_t xc = XB(t, i, c), zc = ZB(t, i, c), xt = XB(t, i, tq), zt = ZB(t, i, tq);
+    t->r[i] ^= (uint8_t)(xc & zt & ((xt ^ zc) ^ 1u));
+    XB(t, i, tq) = (uint8_t)(xt ^ xc);
+    ZB(t, i, c) = (uint8_t)(zc ^ zt);
+  }
+}
+
+/* Pauli gates: conjugation by a Pauli flips the sign of exactly the rows
+ * that anticommute with it on that qubit. */
+static void rule_pauli(chp_t *t, int q, int ax, int az) {
+  /* the gate Pauli is (ax, az); a row Pauli (x, z) anticommutes with it
+   * iff x*az + z*ax is odd */
+  for (int i = 0; i < 2 * t->n; ++i)
+    t->r[i] ^= (uint8_t)((XB(t, i, q) & az) ^ (ZB(t, i, q) & ax));
+}
+
+void oracle_gate(chp_t *t, int type, int a, int b) {
+  switch (type) {
+    case G_I: break;
+    case G_X: rule_pauli(t, a, 1, 0); break;
+    case G_Y: rule_pauli(t, a, 1, 1); break;
+    case G_Z: rule_pauli(t, a, 0, 1); break;
+    case G_H: rule_h(t, a); break;
+    case G_S: rule_p(t, a); break;
+    case G_SDG: rule_p(t, a); rule_p(t, a); rule_p(t, a); break;
+    case G_CX: rule_cx(t, a, b); break;
+    case G_CZ: rule_h(t, b); rule_cx(t, a, b); rule_h(t, b); break;
+    case G_CY: /* S_b^dag, CX, S_b in circuit order */
+      rule_p(t, b); rule_p(t, b); rule_p(t, b); rule_cx(t, a, b); rule_p(t, b); break;
+    case G_SWAP: rule_cx(t, a, b); rule_cx(t, b, a); rule_cx(t, a, b); break;
+    case G_ISWAP: /* CZ, SWAP, S_a, S_b in circuit order */
+      oracle_gate(t, G_CZ, a, b); oracle_gate(t, G_SWAP, a, b); rule_p(t, a); rule_p(t, b); break;
+    default: break;
+  }
+}
+
+/* gates: count rows of (type, q0, q1) */
+void oracle_apply(chp_t *t, const uint32_t *gates, long count) {
+  for (long g = 0; g < count; ++g)
+    oracle_gate(t, (int)gates[3 * g], (int)gates[3 * g + 1], (int)gates[3 * g + 2]);
+}
+
+/* --- rowsum (Aaronson & Gottesman), cited in Sec. 2.5 ------------------ */
+
+/* exponent of i in sigma(x1,z1) * sigma(x2,z2), in {-1, 0, +1} */
+static int g_fn(int x1, int z1, int x2, int z2) {
+  if (x1 == 0 && z1 == 0) return 0;
+  if (x1 == 1 && z1 == 1) return z2 - x2;           /* Y * . */
+  if (x1 == 1 && z1 == 0) return z2 * (2 * x2 - 1); /* X * . */
+  return x2 * (1 - 2 * z2);                         /* Z * . */
+}
+
+/* row h <- row i * row h (generator product), sign from the mod-4 phase */
+static void rowsum(chp_t *t, int h, int i) {
+  int n = t->n;
+  long sum = 2 * (long)t->r[h] + 2 * (long)t->r[i];
+  for (int j = 0; j < n; ++j)
+    sum += g_fn(XB(t, i, j), ZB(t, i, j), XB(t, h, j), ZB(t, h, j));
+  long m = ((sum % 4) + 4) % 4;
+  if (m == 1 || m == 3) t->odd_phase_count++;
+  t->r[h] = (uint8_t)(m == 2);
+  for (int j = 0; j < n; ++j) {
+    XB(t, h, j) ^= XB(t, i, j);
+    ZB(t, h, j) ^= ZB(t, i, j);
+  }
+}
+
+/* --- Z-measurement, Sec. 2.5 "The CHP algorithm" ---------------------- */
+
+/* Measures qubit q. The coin of a probabilistic outcome is
+ * coin(seed, shot, midx), or 0 when force_zero is set (reference record). */
+int oracle_measure(chp_t *t, int q, uint64_t seed, uint64_t shot, uint64_t midx, int force_zero) {
+  int n = t->n;
+  /* probabilistic iff some stabilizer has x_pq = 1; pivot = smallest */
+  int p = -1;
+  for (int i = n; i < 2 * n; ++i)
+    if (XB(t, i, q)) { p = i; break; }
+  if (p >= 0) {
+    t->last_kind = 1;
+    /* 1. make every other anticommuting generator commute: rowsum(i, p) */
+    for (int i = 0; i < 2 * n; ++i)
+      if (i != p && i != p - n && XB(t, i, q)) rowsum(t, i, p);
+    /* 2. D_{p-n} <- S_p */
+    memcpy(&XB(t, p - n, 0), &XB(t, p, 0), (size_t)n);
+    memcpy(&ZB(t, p - n, 0), &ZB(t, p, 0), (size_t)n);
+    t->r[p - n] = t->r[p];
+    /* 3. S_p <- (-1)^m Z_q with a fresh coin m; return m */
+    memset(&XB(t, p, 0), 0, (size_t)n);
+    memset(&ZB(t, p, 0), 0, (size_t)n);
+    ZB(t, p, q) = 1;
+    int m = force_zero ? 0 : oracle_coin(seed, shot, midx);
+    t->r[p] = (uint8_t)m;
+    return m;
+  }
+  /* deterministic: (-1)^m Z_q = product of S_i over i with x_iq(D_i) = 1 */
+  t->last_kind = 0;
+  int s = 2 * n;
+  memset(&XB(t, s, 0), 0, (size_t)n);
+  memset(&ZB(t, s, 0), 0, (size_t)n);
+  t->r[s] = 0;
+  for (int i = 0; i < n; ++i)
+    if (XB(t, i, q)) rowsum(t, s, i + n);
+  for (int j = 0; j < n; ++j)
+    if (XB(t, s, j) != 0 || ZB(t, s, j) != (j == q)) { t->det_check_fail++; break; }
+  return t->r[s];
+}
+
+/* Runs a measurement list in order; record indices start at midx0. */
+void oracle_measure_many(chp_t *t, const uint32_t *qubits, long count, uint64_t seed,
+                         uint64_t shot, uint64_t midx0, int force_zero, uint8_t *out,
+                         uint8_t *kind) {
+  for (long i = 0; i < count; ++i) {
+    out[i] = (uint8_t)oracle_measure(t, (int)qubits[i], seed, shot, midx0 + (uint64_t)i, force_zero);
+    if (kind) kind[i] = (uint8_t)t->last_kind;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Pauli-frame sampling, Sec. 5 (Alg. 9)                                */
+/* ------------------------------------------------------------------ */
+
+/* One frame per shot: fx, fz are shots*n bytes (shot-major). Gates act on
+ * the frame bits by the same rules as the tableau, without signs. */
+static void frame_gate(uint8_t *fx, uint8_t *fz, int type, int a, int b) {
+  uint8_t t8;
+  switch (type) {
+    case G_H: t8 = fx[a]; fx[a] = fz[a]; fz[a] = t8; break;
+    case G_S: case G_SDG: fz[a] ^= fx[a]; break;
+    case G_CX: fx[b] ^= fx[a]; fz[a] ^= fz[b]; break;
+    case G_CZ: frame_gate(fx, fz, G_H, b, 0); frame_gate(fx, fz, G_CX, a, b); frame_gate(fx, fz, G_H, b, 0); break;
+    case G_CY: frame_gate(fx, fz, G_S, b, 0); frame_gate(fx, fz, G_CX, a, b); frame_gate(fx, fz, G_S, b, 0); break;
+    case G_SWAP:
+      t8 = fx[a]; fx[a] = fx[b]; fx[b] = t8;
+      t8 = fz[a]; fz[a] = fz[b]; fz[b] = t8; break;
+    case G_ISWAP:
+      frame_gate(fx, fz, G_CZ, a, b); frame_gate(fx, fz, G_SWAP, a, b);
+      frame_gate(fx, fz, G_S, a, 0); frame_gate(fx, fz, G_S, b, 0); break;
+    default: break; /* I, X, Y, Z change no frame bit */
+  }
+}
+
+/*
+ * Samples `shots` shots of a program given as a list of ops:
+ *   op_kind[o] = 0: apply gates[op_a[o] .. op_b[o]) (rows of 3 uint32)
+ *   op_kind[o] = 1: measure qubits[op_a[o] .. op_b[o]) in order
+ * ref[m] is the reference outcome of measurement m (program order).
+ * out[m * shots + s] = outcome bit of measurement m in shot s.
+ * Frame init: fx = 0, fz[q] = bit (s mod 64) of frame_word(seed, 0, q, s/64);
+ * after measurement m of q: fz[q] = bit of frame_word(seed, m + 1, q, s/64).
+ */
+int oracle_frames(int n, const uint32_t *gates, const uint32_t *qubits, const int *op_kind,
+                  const long *op_a, const long *op_b, long n_ops, const uint8_t *ref,
+                  long shots, uint64_t seed, uint8_t *out) {
+  uint8_t *fx = (uint8_t *)calloc((size_t)n, 1), *fz = (uint8_t *)calloc((size_t)n, 1);
+  if (!fx || !fz) { free(fx); free(fz); return -1; }
+  for (long s = 0; s < shots; ++s) {
+    uint64_t j = (uint64_t)s >> 6, bit = (uint64_t)s & 63u;
+    for (int q = 0; q < n; ++q) {
+      fx[q] = 0;
+      fz[q] = (uint8_t)((oracle_frame_word(seed, 0, (uint64_t)q, j) >> bit) & 1u);
+    }
+    long m = 0;
+    for (long o = 0; o < n_ops; ++o) {
+      if (op_kind[o] == 0) {
+        for (long g = op_a[o]; g < op_b[o]; ++g)
+          frame_gate(fx, fz, (int)gates[3 * g], (int)gates[3 * g + 1], (int)gates[3 * g + 2]);
+      } else {
+        for (long i = op_a[o]; i < op_b[o]; ++i, ++m) {
+          int q = (int)qubits[i];
+          out[(size_t)m * (size_t)shots + (size_t)s] = (uint8_t)(fx[q] ^ ref[m]);
+          fz[q] = (uint8_t)((oracle_frame_word(seed, (uint64_t)m + 1, (uint64_t)q, j) >> bit) & 1u);
+        }
+      }
+    }
+  }
+  free(fx); free(fz);
+  return 0;
+}
