@@ -1,0 +1,228 @@
+/*
+ * qs.h - C ABI of the GB300 stabilizer-tableau simulator (libqs.so).
+ *
+ * The library simulates Clifford circuits with Z-measurements on one GPU
+ * (sm_103a) by Aaronson-Gottesman tableau evolution over a bit-packed
+ * X/Z/sign tableau, following arXiv 2603.14641 ("QuaSARQ"):
+ *   - extended tableau (n destabilizers D_i, n stabilizers S_i), Sec. 2.5 Eq. 7;
+ *   - gate layers by the column update rules of Sec. 2.4 Eq. 4, applied to all
+ *     2n rows word-parallel (Sec. 4.4, Alg. 3);
+ *   - projective Z-measurement by CHP (Sec. 2.5): pivot search, rowsum of the
+ *     pivot into every anticommuting row with the mod-4 phase, and the
+ *     deterministic-outcome product (Sec. 2.5, Sec. 3.2 Eqs. 9-11);
+ *   - many-shot Pauli-frame sampling (Sec. 5, Alg. 9).
+ *
+ * Conventions for every call:
+ *   - Return value: QS_OK (0) or a negative QS_ERR_* code; qs_last_error()
+ *     gives a message for the calling thread. No C++ exception crosses the ABI.
+ *   - Host arrays are owned by the caller and are read (or written) before the
+ *     call returns, except where a call says otherwise.
+ *   - Device memory is owned by the caller when it passes a workspace, else by
+ *     the library (cudaMalloc at create, cudaFree at destroy).
+ *   - All device work is ordered on the stream given at create. Calls that
+ *     return host data synchronise that stream; the others do not.
+ *   - A sim is used by one host thread at a time.
+ *   - On QS_ERR_ARG / QS_ERR_SIZE the sim is unchanged. After QS_ERR_CUDA or
+ *     QS_ERR_INTERNAL the sim is flagged unusable and later calls fail with
+ *     QS_ERR_STATE.
+ */
+#ifndef QS_GB300_API_H_
+#define QS_GB300_API_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QS_OK 0
+#define QS_ERR_ARG (-1)      /* bad argument: qubit >= n, overlapping qubits in a layer, unknown gate */
+#define QS_ERR_OOM (-2)      /* device or host allocation failed */
+#define QS_ERR_CUDA (-3)     /* a CUDA call failed */
+#define QS_ERR_TIMEOUT (-4)  /* a bounded device wait ran out */
+#define QS_ERR_SIZE (-5)     /* output buffer too small or capacity exceeded */
+#define QS_ERR_STATE (-6)    /* the sim is unusable after an earlier device error */
+#define QS_ERR_INTERNAL (-7) /* a device self-check failed (odd rowsum phase, bad deterministic product) */
+
+/* Gate types: the paper's 11-gate Clifford set (Sec. 6 "Benchmarks") plus identity. */
+enum {
+  QS_I = 0, QS_X = 1, QS_Y = 2, QS_Z = 3, QS_H = 4, QS_S = 5, QS_SDG = 6,
+  QS_CX = 7, QS_CY = 8, QS_CZ = 9, QS_SWAP = 10, QS_ISWAP = 11, QS_NUM_GATE_TYPES = 12
+};
+
+/* One gate record. q1 is ignored for one-qubit gates; for CX/CY q0 is the
+ * control and q1 the target. */
+typedef struct qs_gate {
+  uint32_t type;
+  uint32_t q0;
+  uint32_t q1;
+} qs_gate;
+
+/* Key of the counter-based random source (Philox4x64-10, Salmon et al. 2011;
+ * the paper draws Philox numbers through cuRAND, Sec. 5). The coin of the
+ * probabilistic outcome with record index m is bit 0 of word 0 of
+ * Philox(counter = (m, shot, 0, 0), key = (seed, 0x51A7E)). */
+typedef struct qs_key {
+  uint64_t seed;
+  uint64_t shot;
+} qs_key;
+
+typedef struct qs_options {
+  uint64_t record_capacity; /* max measurements kept in the device record; 0 = 16 n + 65536 */
+  uint32_t flags;           /* reserved, 0 */
+  uint32_t reserved;
+} qs_options;
+
+typedef struct qs_sim qs_sim;
+
+/* Layouts for qs_sim_tableau_export. */
+enum {
+  /* Host rows 0..2n-1 (destabilizers, then stabilizers), each ceil(n/64)
+   * x-words then ceil(n/64) z-words (bit j of word w = qubit 64 w + j),
+   * followed by ceil(2n/64) sign words (bit i = sign of row i). */
+  QS_LAYOUT_ROWS_PACKED = 0
+};
+
+/* Library version string. */
+const char *qs_version(void);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char *qs_last_error(void);
+
+/* Device bytes a sim of n qubits needs when the caller supplies the workspace
+ * (tableau in column- and row-major form, scratch and record). */
+size_t qs_sim_required_bytes(uint32_t n, const qs_options *opt);
+
+/*
+ * Creates a sim of n >= 1 qubits in state |0...0> (Sec. 4.1 Alg. 2,
+ * AllocateTableau + InitializeTableau).
+ *   opt:        NULL for defaults.
+ *   cuda_stream: cudaStream_t the sim enqueues on (NULL = legacy default).
+ *   workspace:  device pointer of >= qs_sim_required_bytes(n, opt) bytes,
+ *               256-byte aligned, owned by the caller and kept alive until
+ *               qs_sim_destroy; or NULL to let the library cudaMalloc it.
+ * Errors: QS_ERR_ARG (n == 0 or n > 2^20, unaligned workspace),
+ * QS_ERR_SIZE (workspace too small), QS_ERR_OOM, QS_ERR_CUDA.
+ */
+int qs_sim_create(uint32_t n, const qs_options *opt, void *cuda_stream, void *workspace,
+                  size_t workspace_bytes, qs_sim **out);
+
+/* Waits for the sim's stream, frees what the library allocated. NULL is a no-op. */
+int qs_sim_destroy(qs_sim *sim);
+
+/* Re-initialises the tableau to a computational basis state (Alg. 2 input
+ * initstate): D_i = X_i, S_i = Z_i, and both rows of qubit i get sign
+ * initstate[i] (Sec. 2.5 Eq. 8 pattern). initstate: n bytes (0/1) on the
+ * host, or NULL for |0...0>. Clears the record and the op log. */
+int qs_sim_reset(qs_sim *sim, const uint8_t *initstate);
+
+/*
+ * Applies one layer of gates on pairwise disjoint qubits (a window of
+ * Sec. 4.2) to every tableau row (Sec. 2.4 Eq. 4; Sec. 4.4 Alg. 3).
+ * gates: host array of n_gates records. Validated on the host before any
+ * device work: QS_ERR_ARG for an unknown type, a qubit >= n, q0 == q1 on a
+ * two-qubit gate, or a qubit used twice in the layer. The layer is kept in
+ * the sim's op log for qs_sim_sample.
+ */
+int qs_sim_apply_layer(qs_sim *sim, const qs_gate *gates, uint32_t n_gates);
+
+/*
+ * Validates and packs layered gates into the device record format used by
+ * qs_sim_apply_layers_dev: 2 uint32 per gate, (type << 24 | q0, q1).
+ *   gates:     host records, layer l = gates[layer_ptr[l] .. layer_ptr[l+1]).
+ *   layer_ptr: host array of n_layers + 1 nondecreasing offsets, layer_ptr[0] = 0.
+ *   packed:    host output of 2 * layer_ptr[n_layers] uint32.
+ * Errors: QS_ERR_ARG as qs_sim_apply_layer (message names the layer/gate).
+ */
+int qs_pack_layers(uint32_t n, const qs_gate *gates, const int64_t *layer_ptr, uint32_t n_layers,
+                   uint32_t *packed);
+
+/*
+ * Applies layers l_begin..l_end-1 of a circuit already resident in device
+ * memory (packed by qs_pack_layers for this n and copied to the device by the
+ * caller). packed_dev must stay valid until the work has run and, if
+ * qs_sim_sample will replay it, until the sim is reset or destroyed.
+ * layer_ptr: host offsets as given to qs_pack_layers.
+ */
+int qs_sim_apply_layers_dev(qs_sim *sim, const uint32_t *packed_dev, const int64_t *layer_ptr,
+                            uint32_t l_begin, uint32_t l_end);
+
+/*
+ * Measures qubits in the Z basis, one after another in array order (CHP,
+ * Sec. 2.5; measurement indices continue the sim's record). Each outcome is
+ * appended to the device record. Probabilistic outcomes are the keyed coin of
+ * the measurement's record index; deterministic outcomes follow from the
+ * stabilizer group (Sec. 2.5 Eq. 6).
+ *   qubits:   host array of count qubit indices (< n; repeats allowed).
+ *   outcomes: host array of count bytes to receive the outcomes (0/1), or
+ *             NULL to leave them on the device (no synchronisation).
+ * Errors: QS_ERR_ARG (qubit >= n), QS_ERR_SIZE (record capacity exceeded).
+ */
+int qs_sim_measure(qs_sim *sim, const uint32_t *qubits, uint32_t count, qs_key key,
+                   uint8_t *outcomes);
+
+/* As qs_sim_measure with the qubit list already in device memory (count
+ * uint32, each < n; not checked on the host: an out-of-range qubit makes the
+ * kernels skip the measurement and raise QS_ERR_INTERNAL at the next sync).
+ * The list must stay valid until qs_sim_sample if that will replay it. */
+int qs_sim_measure_dev(qs_sim *sim, const uint32_t *qubits_dev, uint32_t count, qs_key key);
+
+/* Number of measurements in the record. */
+uint64_t qs_sim_num_measurements(const qs_sim *sim);
+
+/* Copies record entries [first, first + count) to host bytes (0/1). Syncs. */
+int qs_sim_record(qs_sim *sim, uint64_t first, uint64_t count, uint8_t *dst);
+
+/* Device bytes of frame workspace qs_sim_sample needs for `shots` shots. */
+size_t qs_sim_sample_required_bytes(const qs_sim *sim, uint64_t shots);
+
+/*
+ * Samples `shots` shots of the program in the sim's op log (every layer and
+ * measurement since create/reset) by Pauli frames (Sec. 5, Alg. 9): frames
+ * start with X~ = 0, Z~ = keyed Philox words; gate layers act on the frames
+ * without signs; measurement m of qubit q outputs X~[q] XOR ref[m] and
+ * re-randomises Z~[q]. The reference ref is the sim's own single-shot record.
+ * Frame words: word j (shots 64 j .. 64 j + 63) of qubit q after event e is
+ * word (j & 3) of Philox(counter = (e, q, j >> 2, 1), key = (seed, 0xF4A3E)),
+ * e = 0 at initialisation and e = m + 1 after measurement m.
+ *   record: [M][ceil(shots/64)] uint64 (M = qs_sim_num_measurements), bit s of
+ *           word j of measurement m = outcome of shot 64 j + s (bits >= shots
+ *           are 0); host or device pointer; record_words >= M * ceil(shots/64).
+ *   frame_ws: device workspace of >= qs_sim_sample_required_bytes bytes, or
+ *           NULL to let the library allocate it for the call.
+ * Syncs the stream when record is a host pointer.
+ */
+int qs_sim_sample(qs_sim *sim, uint64_t shots, uint64_t seed, uint64_t *record,
+                  size_t record_words, void *frame_ws, size_t frame_ws_bytes);
+
+/*
+ * Copies the tableau out in `layout` (QS_LAYOUT_ROWS_PACKED) to host memory.
+ * needed: if not NULL, receives the byte size. dst may be NULL to query.
+ * Errors: QS_ERR_SIZE when dst_bytes is too small. Syncs.
+ */
+int qs_sim_tableau_export(qs_sim *sim, int layout, void *dst, size_t dst_bytes, size_t *needed);
+
+/*
+ * Copies selected generator rows to host memory: rows[i] in 0..2n-1
+ * (0..n-1 destabilizers D_i, n..2n-1 stabilizers S_i, Sec. 2.5 Eq. 7). For
+ * each row dst receives ceil(n/64) x-words, ceil(n/64) z-words (bit j of word
+ * w = qubit 64 w + j) and one word with the sign bit in bit 0, i.e.
+ * count * (2 ceil(n/64) + 1) words. Syncs.
+ * Errors: QS_ERR_ARG (row >= 2n or NULL pointers).
+ */
+int qs_sim_export_rows(qs_sim *sim, const uint32_t *rows, uint32_t count, uint64_t *dst);
+
+/* Waits for the stream and checks the device error flags:
+ * QS_ERR_INTERNAL if a self-check failed, QS_ERR_TIMEOUT if a bounded wait
+ * ran out. */
+int qs_sim_sync(qs_sim *sim);
+
+/* Number of kernel launches the sim has enqueued so far. */
+uint64_t qs_sim_launch_count(const qs_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_GB300_API_H_ */

@@ -94,6 +94,7 @@ enum { G_I, G_X, G_Y, G_Z, G_H, G_S, G_SDG, G_CX, G_CY, G_CZ, G_SWAP, G_ISWAP };
 
 typedef struct {
   int n;
+  int rows;   /* rows the gate rules act on: 2n, or the size of a row subset */
   uint8_t *x; /* (2n+1) rows of n bits; row 2n is the scratch row */
   uint8_t *z;
   uint8_t *r; /* 2n+1 sign bits */
@@ -124,6 +125,7 @@ chp_t *oracle_new(int n) {
   chp_t *t = (chp_t *)calloc(1, sizeof(chp_t));
   if (!t) return NULL;
   t->n = n;
+  t->rows = 2 * n;
   size_t cells = (size_t)(2 * n + 1) * (size_t)(n > 0 ? n : 1);
   t->x = (uint8_t *)calloc(cells, 1);
   t->z = (uint8_t *)calloc(cells, 1);
@@ -131,6 +133,36 @@ chp_t *oracle_new(int n) {
   if (!t->x || !t->z || !t->r) { free(t->x); free(t->z); free(t->r); free(t); return NULL; }
   oracle_reset(t, NULL);
   return t;
+}
+
+/* A subset of generator rows evolved under gates only. Gate rules act on
+ * each row independently (Sec. 2.4: the rules apply to every row index i), so
+ * rows row_ids[0..nr) (0..n-1 destabilizers, n..2n-1 stabilizers) of the
+ * full tableau can be followed alone; row j of this object is row row_ids[j]
+ * of the initial tableau |0...0>. */
+chp_t *oracle_new_subset(int n, const uint32_t *row_ids, int nr) {
+  chp_t *t = (chp_t *)calloc(1, sizeof(chp_t));
+  if (!t) return NULL;
+  t->n = n;
+  t->rows = nr;
+  size_t cells = (size_t)(nr + 1) * (size_t)n;
+  t->x = (uint8_t *)calloc(cells, 1);
+  t->z = (uint8_t *)calloc(cells, 1);
+  t->r = (uint8_t *)calloc((size_t)nr + 1, 1);
+  if (!t->x || !t->z || !t->r) { free(t->x); free(t->z); free(t->r); free(t); return NULL; }
+  for (int j = 0; j < nr; ++j) {
+    uint32_t g = row_ids[j];
+    if (g < (uint32_t)n) XB(t, j, g) = 1;
+    else ZB(t, j, g - (uint32_t)n) = 1;
+  }
+  t->last_kind = -1;
+  return t;
+}
+
+/* Copies out the rows of a subset object: x, z are nr*n bytes, r is nr bytes. */
+void oracle_get_subset(const chp_t *t, uint8_t *x, uint8_t *z, uint8_t *r) {
+  size_t cells = (size_t)t->rows * t->n;
+  memcpy(x, t->x, cells); memcpy(z, t->z, cells); memcpy(r, t->r, (size_t)t->rows);
 }
 
 void oracle_free(chp_t *t) {
@@ -156,7 +188,7 @@ void oracle_set(chp_t *t, const uint8_t *x, const uint8_t *z, const uint8_t *r) 
 /* --- Sec. 2.4, Eq. 4: the three base rules, applied to every row ------- */
 
 static void rule_h(chp_t *t, int q) {
-  for (int i = 0; i < 2 * t->n; ++i) {
+  for (int i = 0; i < t->rows; ++i) {
     uint8_t x = XB(t, i, q), z = ZB(t, i, q);
     t->r[i] ^= (uint8_t)(x & z);
     XB(t, i, q) = z;
@@ -165,7 +197,7 @@ static void rule_h(chp_t *t, int q) {
 }
 
 static void rule_p(chp_t *t, int q) {
-  for (int i = 0; i < 2 * t->n; ++i) {
+  for (int i = 0; i < t->rows; ++i) {
     uint8_t x = XB(t, i, q), z = ZB(t, i, q);
     t->r[i] ^= (uint8_t)(x & z);
     ZB(t, i, q) = (uint8_t)(z ^ x);
@@ -173,7 +205,7 @@ static void rule_p(chp_t *t, int q) {
 }
 
 static void rule_cx(chp_t *t, int c, int tq) {
-  for (int i = 0; i < 2 * t->n; ++i) {
+  for (int i = 0; i < t->rows; ++i) {
     uint8_t xc = XB(t, i, c), zc = ZB(t, i, c), xt = XB(t, i, tq), zt = ZB(t, i, tq);
     t->r[i] ^= (uint8_t)(xc & zt & ((xt ^ zc) ^ 1u));
     XB(t, i, tq) = (uint8_t)(xt ^ xc);
@@ -186,7 +218,7 @@ static void rule_cx(chp_t *t, int c, int tq) {
 static void rule_pauli(chp_t *t, int q, int ax, int az) {
   /* the gate Pauli is (ax, az); a row Pauli (x, z) anticommutes with it
    * iff x*az + z*ax is odd */
-  for (int i = 0; i < 2 * t->n; ++i)
+  for (int i = 0; i < t->rows; ++i)
     t->r[i] ^= (uint8_t)((XB(t, i, q) & az) ^ (ZB(t, i, q) & ax));
 }
 
@@ -247,6 +279,7 @@ static void rowsum(chp_t *t, int h, int i) {
  * coin(seed, shot, midx), or 0 when force_zero is set (reference record). */
 int oracle_measure(chp_t *t, int q, uint64_t seed, uint64_t shot, uint64_t midx, int force_zero) {
   int n = t->n;
+  if (t->rows != 2 * n) return -1; /* a row subset cannot be measured */
   /* probabilistic iff some stabilizer has x_pq = 1; pivot = smallest */
   int p = -1;
   for (int i = n; i < 2 * n; ++i)

@@ -65,6 +65,9 @@ def lib():
         L.oracle_det_check_fail.argtypes = [ctypes.c_void_p]
         L.oracle_last_kind.restype = ctypes.c_int
         L.oracle_last_kind.argtypes = [ctypes.c_void_p]
+        L.oracle_new_subset.restype = ctypes.c_void_p
+        L.oracle_new_subset.argtypes = [ctypes.c_int, _u32p, ctypes.c_int]
+        L.oracle_get_subset.argtypes = [ctypes.c_void_p, _u8p, _u8p, _u8p]
         L.oracle_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
         L.oracle_coin.restype = ctypes.c_int
         L.oracle_coin.argtypes = [ctypes.c_uint64] * 3
@@ -167,6 +170,38 @@ class Oracle:
     @property
     def det_check_fail(self) -> int:
         return int(lib().oracle_det_check_fail(self._h))
+
+
+class RowSubset:
+    """Chosen generator rows of the n-qubit tableau, evolved under gates only
+    (gate rules act row by row, Sec. 2.4). rows: ids in 0..2n-1 (destabilizers
+    0..n-1, stabilizers n..2n-1) of the initial tableau |0...0>."""
+
+    def __init__(self, n: int, rows):
+        self.n = int(n)
+        self.rows = np.ascontiguousarray(rows, np.uint32)
+        self._h = lib().oracle_new_subset(self.n, _p(self.rows, _u32p), len(self.rows))
+        if not self._h:
+            raise MemoryError("oracle_new_subset failed")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().oracle_free(h)
+            self._h = None
+
+    def apply(self, gates: np.ndarray) -> None:
+        g = np.ascontiguousarray(gates, np.uint32)
+        if g.size:
+            lib().oracle_apply(self._h, _p(g, _u32p), g.shape[0])
+
+    def get(self):
+        nr = len(self.rows)
+        x = np.zeros((nr, self.n), np.uint8)
+        z = np.zeros((nr, self.n), np.uint8)
+        r = np.zeros(nr, np.uint8)
+        lib().oracle_get_subset(self._h, _p(x, _u8p), _p(z, _u8p), _p(r, _u8p))
+        return x, z, r
 
 
 def run_circuit(circuit, seed: int, shot: int = 0, force_zero: bool = False,

@@ -1,0 +1,123 @@
+// Internal declarations shared by the kernels and the C-ABI runtime of libqs.
+//
+// Memory layout in HBM (one sim of n qubits, k = ceil(n/64)):
+//   Column-major tableau (gate layers, Sec. 4.3 "Memory Layout"):
+//     X[q][w], Z[q][w] for q < ncols (= n rounded up to 256), w < cs
+//     (cs = 2k rounded up to 4 words). Bit b of word w is packed row 64 w + b.
+//     Packed rows: destabilizer D_i is row i, stabilizer S_i is row 64 k + i;
+//     the remaining packed rows are zero padding and stay zero under every gate.
+//   Signs S[w], w < cs: bit b of word w = sign bit of packed row 64 w + b
+//     (forward, per-generator signs; untouched by the transposes).
+//   Row-major tableau (measurement, Sec. 4.3): RX[r][u], RZ[r][u] for packed
+//     row r < 64 cs and u < rs (= ncols / 64); bit j of word u = qubit 64 u + j.
+// All words are 64-bit; column and row starts are 32-byte aligned so that
+// 128-bit vector accesses are aligned.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qs.h"
+
+namespace qs {
+
+constexpr int kDetBlocks = 152;     // chunks of the deterministic product (one per SM)
+constexpr int kMeasStateWords = 16; // per-measurement device state
+
+// device error flags (sticky, cleared by reset)
+enum : uint32_t {
+  kErrOddPhase = 1u,    // a rowsum produced an odd power of i
+  kErrDetProduct = 2u,  // deterministic product was not +-Z_q
+  kErrBadGate = 4u,     // packed gate with out-of-range qubit or type
+  kErrBadQubit = 8u,    // measured qubit out of range
+  kErrTimeout = 16u,    // a bounded device wait ran out
+};
+
+// measurement state words (device), indices into MeasState array
+enum : int {
+  kMsPivot = 0,      // packed pivot row (int64), or INT64_MAX if none
+  kMsDetCross = 1,   // XOR of cross parities from the combine pass
+  kMsDetXZ = 2,      // sum of popc(Xtot & Ztot) (must be 0)
+};
+
+struct Layout {
+  uint32_t n, k, cs, ncols, rs;
+  uint64_t nrows;  // 64 * cs
+};
+
+inline Layout make_layout(uint32_t n) {
+  Layout L;
+  L.n = n;
+  L.k = (n + 63) / 64;
+  L.cs = ((2 * L.k) + 3) / 4 * 4;
+  L.ncols = (n + 255) / 256 * 256;
+  L.rs = L.ncols / 64;
+  L.nrows = 64ull * L.cs;
+  return L;
+}
+
+// ------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): device implementation.
+// ------------------------------------------------------------------------
+struct P4 { uint64_t v[4]; };
+
+__device__ __forceinline__ P4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                             uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+    uint64_t hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
+    uint64_t hi1 = __umul64hi(m1, c2), lo1 = m1 * c2;
+    uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B97F4A7C15ull;
+    k1 += 0xBB67AE8584CAA73Bull;
+  }
+  P4 o; o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+  return o;
+}
+
+constexpr uint64_t kCoinKey = 0x51A7Eull;
+constexpr uint64_t kFrameKey = 0xF4A3Eull;
+
+// ------------------------------------------------------------------------
+// Launchers (each returns cudaGetLastError() after the launch).
+// ------------------------------------------------------------------------
+struct Dev {
+  Layout L;
+  uint64_t *X, *Z, *S;     // column-major tableau + signs
+  uint64_t *RX, *RZ;       // row-major tableau
+  uint32_t *colx;          // gathered x column, 2 * cs uint32 (= cs words)
+  int64_t *mst;            // measurement state (kMeasStateWords)
+  uint64_t *det_x, *det_z; // kDetBlocks * rs words each
+  int32_t *det_scal;       // kDetBlocks partial phase sums
+  uint32_t *err;           // sticky error flags
+  uint8_t *record;         // record bytes
+  uint64_t record_cap;
+  int sms;                 // multiprocessor count of the device
+};
+
+cudaError_t launch_init(const Dev &d, const uint8_t *initstate_dev, cudaStream_t s);
+cudaError_t launch_gate_layer(const Dev &d, const uint32_t *packed, uint32_t n_gates,
+                              cudaStream_t s);
+// frames: column-major frame matrices FX/FZ [n][fw] words (fw multiple of 2)
+cudaError_t launch_frame_layer(uint64_t *FX, uint64_t *FZ, uint32_t n, uint32_t fw,
+                               const uint32_t *packed, uint32_t n_gates, uint32_t *err,
+                               cudaStream_t s);
+cudaError_t launch_to_rows(const Dev &d, cudaStream_t s);
+cudaError_t launch_to_cols(const Dev &d, cudaStream_t s);
+// one Z-measurement of qubits[i] with record index midx
+cudaError_t launch_measure_one(const Dev &d, const uint32_t *qubits, uint32_t i, uint64_t midx,
+                               qs_key key, cudaStream_t s, int *launches);
+cudaError_t launch_frame_init(uint64_t *FX, uint64_t *FZ, uint32_t n, uint32_t fw, uint64_t seed,
+                              cudaStream_t s);
+cudaError_t launch_frame_measure(uint64_t *FX, uint64_t *FZ, uint32_t n, uint32_t fw,
+                                 const uint32_t *qubits, uint32_t count, uint64_t m0,
+                                 const uint8_t *ref, uint64_t *out, uint64_t shots, uint64_t seed,
+                                 uint32_t *err, cudaStream_t s);
+cudaError_t launch_reset_meas_state(const Dev &d, cudaStream_t s);
+
+}  // namespace qs

@@ -1,0 +1,667 @@
+// C-ABI runtime of libqs: sim lifetime, device workspace, host-side
+// validation, staging of host inputs, layout switching between the
+// column-major (gates) and row-major (measurement) tableau, the op log that
+// qs_sim_sample replays, and tableau export. Declarations and the contract of
+// every entry point are in include/qs.h.
+//
+// Control flow follows Alg. 2 of the paper (Sec. 4.1): windows of gates are
+// applied with one kernel each; a measurement window first switches the
+// tableau to row-major (Alg. 4) and then runs the measurements in order. The
+// layout switch is lazy: each layout is rebuilt only when the other one has
+// been modified since.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qs_internal.cuh"
+
+using namespace qs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+struct Op {
+  enum Kind { kHostLayer, kDevLayers, kHostMeasure, kDevMeasure } kind;
+  std::vector<uint32_t> packed;  // kHostLayer: 2 words per gate
+  const uint32_t *dev = nullptr; // kDevLayers: packed gates; kDevMeasure: qubit list
+  std::vector<int64_t> ptr;      // kDevLayers: offsets of the replayed layers (+1)
+  std::vector<uint32_t> qubits;  // kHostMeasure
+  uint32_t count = 0;            // kDevMeasure
+  uint64_t m0 = 0;               // first record index of a measurement op
+};
+
+constexpr int kRing = 4;
+constexpr uint32_t kMaxQubits = 1u << 20;
+
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+struct Plan {
+  size_t X, Z, RX, RZ, S, colx, mst, detx, detz, dets, err, record, stage, total;
+  uint64_t record_cap;
+  size_t stage_bytes;
+};
+
+Plan make_plan(const Layout &L, const qs_options *opt) {
+  Plan p;
+  Carve c;
+  p.record_cap = (opt && opt->record_capacity) ? opt->record_capacity : 16ull * L.n + 65536;
+  p.stage_bytes = std::max<size_t>(8ull * (L.n + 64), 256 * 1024);
+  const size_t colb = (size_t)L.ncols * L.cs * 8, rowb = (size_t)L.nrows * L.rs * 8;
+  p.X = c.take(colb);
+  p.Z = c.take(colb);
+  p.RX = c.take(rowb);
+  p.RZ = c.take(rowb);
+  p.S = c.take((size_t)L.cs * 8);
+  p.colx = c.take((size_t)L.cs * 8);
+  p.mst = c.take(kMeasStateWords * 8);
+  p.detx = c.take((size_t)kDetBlocks * L.rs * 8);
+  p.detz = c.take((size_t)kDetBlocks * L.rs * 8);
+  p.dets = c.take((size_t)kDetBlocks * 4);
+  p.err = c.take(4);
+  p.record = c.take(p.record_cap);
+  p.stage = c.take(p.stage_bytes);
+  p.total = c.off;
+  return p;
+}
+
+bool is_two(uint32_t t) { return t >= QS_CX && t <= QS_ISWAP; }
+
+}  // namespace
+
+struct qs_sim {
+  Dev d{};
+  Plan plan{};
+  cudaStream_t stream = nullptr;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  bool owns_ws = false;
+  bool cols_valid = true, rows_valid = false;
+  bool broken = false;
+  uint64_t n_meas = 0;
+  uint8_t *dstage = nullptr;
+  uint8_t *hstage[kRing] = {};
+  cudaEvent_t ev[kRing] = {};
+  int ring = 0;
+  std::vector<Op> ops;
+  std::vector<uint32_t> stamp;
+  uint32_t stamp_id = 0;
+  uint64_t launches = 0;
+};
+
+namespace {
+
+int cuda_fail(qs_sim *s, cudaError_t e, const char *what) {
+  if (s) s->broken = true;
+  return fail(QS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define QS_CUDA(sim, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(sim, e_, #call); \
+  } while (0)
+
+// Next pinned host slot, waiting until its previous copy has finished.
+uint8_t *ring_slot(qs_sim *s, int *slot) {
+  int i = s->ring;
+  s->ring = (s->ring + 1) % kRing;
+  if (cudaEventSynchronize(s->ev[i]) != cudaSuccess) return nullptr;
+  *slot = i;
+  return s->hstage[i];
+}
+
+// Copies `bytes` (<= stage_bytes) from a pinned slot to the device staging area.
+int upload(qs_sim *s, int slot, size_t bytes) {
+  QS_CUDA(s, cudaMemcpyAsync(s->dstage, s->hstage[slot], bytes, cudaMemcpyHostToDevice, s->stream));
+  QS_CUDA(s, cudaEventRecord(s->ev[slot], s->stream));
+  return QS_OK;
+}
+
+int check_usable(qs_sim *s) {
+  if (!s) return fail(QS_ERR_ARG, "sim is NULL");
+  if (s->broken) return fail(QS_ERR_STATE, "sim is unusable after an earlier device error");
+  return QS_OK;
+}
+
+int ensure_cols(qs_sim *s) {
+  if (!s->cols_valid) {
+    QS_CUDA(s, launch_to_cols(s->d, s->stream));
+    s->launches += 2;
+    s->cols_valid = true;
+  }
+  return QS_OK;
+}
+
+int ensure_rows(qs_sim *s) {
+  if (!s->rows_valid) {
+    QS_CUDA(s, launch_to_rows(s->d, s->stream));
+    s->launches += 2;
+    s->rows_valid = true;
+  }
+  return QS_OK;
+}
+
+// Validates one layer; packs into out (2 words per gate). Returns QS_OK or QS_ERR_ARG.
+int validate_pack(uint32_t n, const qs_gate *g, size_t count, std::vector<uint32_t> &stamp,
+                  uint32_t &stamp_id, uint32_t *out, const char *where) {
+  if (stamp.size() < n) stamp.assign(n, 0);
+  if (++stamp_id == 0) {
+    std::fill(stamp.begin(), stamp.end(), 0);
+    stamp_id = 1;
+  }
+  char buf[160];
+  for (size_t i = 0; i < count; ++i) {
+    const uint32_t t = g[i].type, a = g[i].q0, b = g[i].q1;
+    if (t >= QS_NUM_GATE_TYPES) {
+      snprintf(buf, sizeof buf, "%s gate %zu: unknown gate type %u", where, i, t);
+      return fail(QS_ERR_ARG, buf);
+    }
+    if (a >= n || (is_two(t) && b >= n)) {
+      snprintf(buf, sizeof buf, "%s gate %zu: qubit out of range (n = %u)", where, i, n);
+      return fail(QS_ERR_ARG, buf);
+    }
+    if (is_two(t) && a == b) {
+      snprintf(buf, sizeof buf, "%s gate %zu: two-qubit gate on one qubit %u", where, i, a);
+      return fail(QS_ERR_ARG, buf);
+    }
+    if (stamp[a] == stamp_id || (is_two(t) && stamp[b] == stamp_id)) {
+      snprintf(buf, sizeof buf, "%s gate %zu: qubit used twice in one layer", where, i);
+      return fail(QS_ERR_ARG, buf);
+    }
+    stamp[a] = stamp_id;
+    if (is_two(t)) stamp[b] = stamp_id;
+    out[2 * i] = (t << 24) | a;
+    out[2 * i + 1] = is_two(t) ? b : 0;
+  }
+  return QS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qs_version(void) { return "qs-gb300 0.1 (sm_103a)"; }
+
+const char *qs_last_error(void) { return g_last_error.c_str(); }
+
+size_t qs_sim_required_bytes(uint32_t n, const qs_options *opt) {
+  if (n == 0 || n > kMaxQubits) return 0;
+  return make_plan(make_layout(n), opt).total;
+}
+
+int qs_sim_create(uint32_t n, const qs_options *opt, void *cuda_stream, void *workspace,
+                  size_t workspace_bytes, qs_sim **out) {
+  if (!out) return fail(QS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n == 0 || n > kMaxQubits) return fail(QS_ERR_ARG, "n must be in [1, 2^20]");
+  if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(QS_ERR_ARG, "workspace must be 256-byte aligned");
+  qs_sim *s = new (std::nothrow) qs_sim();
+  if (!s) return fail(QS_ERR_OOM, "host allocation failed");
+  s->d.L = make_layout(n);
+  s->plan = make_plan(s->d.L, opt);
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (workspace) {
+    if (workspace_bytes < s->plan.total) {
+      delete s;
+      return fail(QS_ERR_SIZE, "workspace smaller than qs_sim_required_bytes");
+    }
+    s->ws = workspace;
+  } else {
+    cudaError_t e = cudaMalloc(&s->ws, s->plan.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete s;
+      return fail(QS_ERR_OOM, std::string("cudaMalloc of the tableau failed: ") + cudaGetErrorString(e));
+    }
+    s->owns_ws = true;
+  }
+  s->ws_bytes = s->plan.total;
+  uint8_t *b = static_cast<uint8_t *>(s->ws);
+  const Plan &p = s->plan;
+  s->d.X = reinterpret_cast<uint64_t *>(b + p.X);
+  s->d.Z = reinterpret_cast<uint64_t *>(b + p.Z);
+  s->d.RX = reinterpret_cast<uint64_t *>(b + p.RX);
+  s->d.RZ = reinterpret_cast<uint64_t *>(b + p.RZ);
+  s->d.S = reinterpret_cast<uint64_t *>(b + p.S);
+  s->d.colx = reinterpret_cast<uint32_t *>(b + p.colx);
+  s->d.mst = reinterpret_cast<int64_t *>(b + p.mst);
+  s->d.det_x = reinterpret_cast<uint64_t *>(b + p.detx);
+  s->d.det_z = reinterpret_cast<uint64_t *>(b + p.detz);
+  s->d.det_scal = reinterpret_cast<int32_t *>(b + p.dets);
+  s->d.err = reinterpret_cast<uint32_t *>(b + p.err);
+  s->d.record = b + p.record;
+  s->d.record_cap = p.record_cap;
+  s->dstage = b + p.stage;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  s->d.sms = 152;
+  cudaDeviceGetAttribute(&s->d.sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int i = 0; i < kRing; ++i) {
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&s->hstage[i]), p.stage_bytes,
+                                  cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      qs_sim_destroy(s);
+      return fail(QS_ERR_OOM, std::string("pinned staging allocation failed: ") + cudaGetErrorString(e));
+    }
+  }
+  int rc = qs_sim_reset(s, nullptr);
+  if (rc != QS_OK) {
+    std::string msg = g_last_error;
+    qs_sim_destroy(s);
+    return fail(rc, msg);
+  }
+  *out = s;
+  return QS_OK;
+}
+
+int qs_sim_destroy(qs_sim *s) {
+  if (!s) return QS_OK;
+  cudaStreamSynchronize(s->stream);
+  for (int i = 0; i < kRing; ++i) {
+    if (s->ev[i]) cudaEventDestroy(s->ev[i]);
+    if (s->hstage[i]) cudaFreeHost(s->hstage[i]);
+  }
+  if (s->owns_ws && s->ws) cudaFree(s->ws);
+  delete s;
+  return QS_OK;
+}
+
+int qs_sim_reset(qs_sim *s, const uint8_t *initstate) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  const uint32_t n = s->d.L.n;
+  const uint8_t *init_dev = nullptr;
+  if (initstate) {
+    int slot;
+    uint8_t *h = ring_slot(s, &slot);
+    if (!h) return cuda_fail(s, cudaGetLastError(), "staging event");
+    for (uint32_t i = 0; i < n; ++i) h[i] = initstate[i] ? 1 : 0;
+    if ((rc = upload(s, slot, n))) return rc;
+    init_dev = s->dstage;
+  }
+  QS_CUDA(s, cudaMemsetAsync(s->d.err, 0, 4, s->stream));
+  QS_CUDA(s, launch_init(s->d, init_dev, s->stream));
+  QS_CUDA(s, launch_reset_meas_state(s->d, s->stream));
+  s->launches += 3;
+  s->cols_valid = true;
+  s->rows_valid = false;
+  s->n_meas = 0;
+  s->ops.clear();
+  return QS_OK;
+}
+
+int qs_sim_apply_layer(qs_sim *s, const qs_gate *gates, uint32_t n_gates) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (n_gates && !gates) return fail(QS_ERR_ARG, "gates is NULL");
+  if (n_gates > s->d.L.n) return fail(QS_ERR_ARG, "more gates than qubits in one layer");
+  Op op;
+  op.kind = Op::kHostLayer;
+  op.packed.resize(2 * (size_t)n_gates);
+  if ((rc = validate_pack(s->d.L.n, gates, n_gates, s->stamp, s->stamp_id, op.packed.data(),
+                          "layer")))
+    return rc;
+  if (n_gates == 0) return QS_OK;
+  if ((rc = ensure_cols(s))) return rc;
+  int slot;
+  uint8_t *h = ring_slot(s, &slot);
+  if (!h) return cuda_fail(s, cudaGetLastError(), "staging event");
+  memcpy(h, op.packed.data(), op.packed.size() * 4);
+  if ((rc = upload(s, slot, op.packed.size() * 4))) return rc;
+  QS_CUDA(s, launch_gate_layer(s->d, reinterpret_cast<const uint32_t *>(s->dstage), n_gates,
+                               s->stream));
+  s->launches += 1;
+  s->rows_valid = false;
+  s->ops.push_back(std::move(op));
+  return QS_OK;
+}
+
+int qs_pack_layers(uint32_t n, const qs_gate *gates, const int64_t *layer_ptr, uint32_t n_layers,
+                   uint32_t *packed) {
+  if (n == 0 || n > kMaxQubits) return fail(QS_ERR_ARG, "n must be in [1, 2^20]");
+  if (!layer_ptr || (n_layers && (!gates && layer_ptr[n_layers] > 0)) || !packed)
+    return fail(QS_ERR_ARG, "NULL argument");
+  if (layer_ptr[0] != 0) return fail(QS_ERR_ARG, "layer_ptr[0] must be 0");
+  std::vector<uint32_t> stamp;
+  uint32_t sid = 0;
+  for (uint32_t l = 0; l < n_layers; ++l) {
+    const int64_t a = layer_ptr[l], b = layer_ptr[l + 1];
+    if (b < a) return fail(QS_ERR_ARG, "layer_ptr must be nondecreasing");
+    if (b - a > (int64_t)n) return fail(QS_ERR_ARG, "more gates than qubits in one layer");
+    char where[48];
+    snprintf(where, sizeof where, "layer %u", l);
+    int rc = validate_pack(n, gates + a, (size_t)(b - a), stamp, sid, packed + 2 * a, where);
+    if (rc) return rc;
+  }
+  return QS_OK;
+}
+
+int qs_sim_apply_layers_dev(qs_sim *s, const uint32_t *packed_dev, const int64_t *layer_ptr,
+                            uint32_t l_begin, uint32_t l_end) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (!packed_dev || !layer_ptr) return fail(QS_ERR_ARG, "NULL argument");
+  if (l_end < l_begin) return fail(QS_ERR_ARG, "l_end < l_begin");
+  if (l_end == l_begin) return QS_OK;
+  if ((rc = ensure_cols(s))) return rc;
+  Op op;
+  op.kind = Op::kDevLayers;
+  op.dev = packed_dev;
+  op.ptr.assign(layer_ptr + l_begin, layer_ptr + l_end + 1);
+  for (uint32_t l = l_begin; l < l_end; ++l) {
+    const int64_t a = layer_ptr[l], cnt = layer_ptr[l + 1] - a;
+    if (cnt < 0 || cnt > (int64_t)s->d.L.n) return fail(QS_ERR_ARG, "bad layer_ptr");
+    QS_CUDA(s, launch_gate_layer(s->d, packed_dev + 2 * a, (uint32_t)cnt, s->stream));
+    if (cnt) s->launches += 1;
+  }
+  s->rows_valid = false;
+  s->ops.push_back(std::move(op));
+  return QS_OK;
+}
+
+static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint64_t m0, qs_key key) {
+  for (uint32_t i = 0; i < count; ++i) {
+    int l = 0;
+    QS_CUDA(s, launch_measure_one(s->d, qdev, i, m0 + i, key, s->stream, &l));
+    s->launches += (uint64_t)l;
+  }
+  return QS_OK;
+}
+
+int qs_sim_measure(qs_sim *s, const uint32_t *qubits, uint32_t count, qs_key key,
+                   uint8_t *outcomes) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (count && !qubits) return fail(QS_ERR_ARG, "qubits is NULL");
+  for (uint32_t i = 0; i < count; ++i)
+    if (qubits[i] >= s->d.L.n) {
+      char buf[96];
+      snprintf(buf, sizeof buf, "measured qubit %u out of range (n = %u)", qubits[i], s->d.L.n);
+      return fail(QS_ERR_ARG, buf);
+    }
+  if (s->n_meas + count > s->d.record_cap)
+    return fail(QS_ERR_SIZE, "record capacity exceeded (qs_options.record_capacity)");
+  if (count == 0) return QS_OK;
+  if ((rc = ensure_rows(s))) return rc;
+  const uint64_t m0 = s->n_meas;
+  const uint32_t chunk = (uint32_t)(s->plan.stage_bytes / 4);
+  for (uint32_t off = 0; off < count; off += chunk) {
+    const uint32_t c = std::min(chunk, count - off);
+    int slot;
+    uint8_t *h = ring_slot(s, &slot);
+    if (!h) return cuda_fail(s, cudaGetLastError(), "staging event");
+    memcpy(h, qubits + off, (size_t)c * 4);
+    if ((rc = upload(s, slot, (size_t)c * 4))) return rc;
+    if ((rc = measure_staged(s, reinterpret_cast<const uint32_t *>(s->dstage), c, m0 + off, key)))
+      return rc;
+  }
+  s->n_meas += count;
+  s->cols_valid = false;
+  Op op;
+  op.kind = Op::kHostMeasure;
+  op.qubits.assign(qubits, qubits + count);
+  op.m0 = m0;
+  s->ops.push_back(std::move(op));
+  if (outcomes) {
+    QS_CUDA(s, cudaMemcpyAsync(outcomes, s->d.record + m0, count, cudaMemcpyDeviceToHost, s->stream));
+    return qs_sim_sync(s);
+  }
+  return QS_OK;
+}
+
+int qs_sim_measure_dev(qs_sim *s, const uint32_t *qubits_dev, uint32_t count, qs_key key) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (count && !qubits_dev) return fail(QS_ERR_ARG, "qubits_dev is NULL");
+  if (s->n_meas + count > s->d.record_cap)
+    return fail(QS_ERR_SIZE, "record capacity exceeded (qs_options.record_capacity)");
+  if (count == 0) return QS_OK;
+  if ((rc = ensure_rows(s))) return rc;
+  const uint64_t m0 = s->n_meas;
+  if ((rc = measure_staged(s, qubits_dev, count, m0, key))) return rc;
+  s->n_meas += count;
+  s->cols_valid = false;
+  Op op;
+  op.kind = Op::kDevMeasure;
+  op.dev = qubits_dev;
+  op.count = count;
+  op.m0 = m0;
+  s->ops.push_back(std::move(op));
+  return QS_OK;
+}
+
+uint64_t qs_sim_num_measurements(const qs_sim *s) { return s ? s->n_meas : 0; }
+
+uint64_t qs_sim_launch_count(const qs_sim *s) { return s ? s->launches : 0; }
+
+int qs_sim_record(qs_sim *s, uint64_t first, uint64_t count, uint8_t *dst) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (first + count > s->n_meas) return fail(QS_ERR_ARG, "record range beyond the measurements");
+  if (count && !dst) return fail(QS_ERR_ARG, "dst is NULL");
+  if (count)
+    QS_CUDA(s, cudaMemcpyAsync(dst, s->d.record + first, count, cudaMemcpyDeviceToHost, s->stream));
+  return qs_sim_sync(s);
+}
+
+int qs_sim_sync(qs_sim *s) {
+  if (!s) return fail(QS_ERR_ARG, "sim is NULL");
+  if (s->broken) return fail(QS_ERR_STATE, "sim is unusable after an earlier device error");
+  QS_CUDA(s, cudaStreamSynchronize(s->stream));
+  uint32_t flags = 0;
+  QS_CUDA(s, cudaMemcpy(&flags, s->d.err, 4, cudaMemcpyDeviceToHost));
+  if (flags & kErrTimeout) {
+    s->broken = true;
+    return fail(QS_ERR_TIMEOUT, "a bounded device wait ran out");
+  }
+  if (flags) {
+    s->broken = true;
+    char buf[128];
+    snprintf(buf, sizeof buf, "device self-check failed (flags 0x%x: odd phase=1, det=2, gate=4, qubit=8)",
+             flags);
+    return fail(QS_ERR_INTERNAL, buf);
+  }
+  return QS_OK;
+}
+
+static size_t sample_bytes(const qs_sim *s, uint64_t shots, uint64_t *fw_out, uint64_t *ow_out) {
+  const uint64_t ow = (shots + 63) / 64;
+  const uint64_t fw = (ow + 3) / 4 * 4;
+  if (fw_out) *fw_out = fw;
+  if (ow_out) *ow_out = ow;
+  Carve c;
+  c.take((size_t)s->d.L.n * fw * 8);
+  c.take((size_t)s->d.L.n * fw * 8);
+  c.take((size_t)std::max<uint64_t>(1, s->n_meas) * ow * 8);  // device record if output is host
+  return c.off;
+}
+
+size_t qs_sim_sample_required_bytes(const qs_sim *s, uint64_t shots) {
+  if (!s || shots == 0) return 0;
+  return sample_bytes(s, shots, nullptr, nullptr);
+}
+
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, size_t record_words,
+                  void *frame_ws, size_t frame_ws_bytes) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (shots == 0) return fail(QS_ERR_ARG, "shots must be positive");
+  uint64_t fw, ow;
+  const size_t need = sample_bytes(s, shots, &fw, &ow);
+  if (fw > 0xFFFFFFFFull) return fail(QS_ERR_ARG, "too many shots");
+  const uint64_t M = s->n_meas;
+  if (M && !record) return fail(QS_ERR_ARG, "record is NULL");
+  if (record_words < M * ow) return fail(QS_ERR_SIZE, "record smaller than M * ceil(shots/64) words");
+  if (frame_ws && frame_ws_bytes < need) return fail(QS_ERR_SIZE, "frame workspace too small");
+  bool own = false;
+  void *ws = frame_ws;
+  if (!ws) {
+    QS_CUDA(s, cudaMallocAsync(&ws, need, s->stream));
+    own = true;
+  }
+  Carve c;
+  uint8_t *b = static_cast<uint8_t *>(ws);
+  const uint32_t n = s->d.L.n;
+  uint64_t *FX = reinterpret_cast<uint64_t *>(b + c.take((size_t)n * fw * 8));
+  uint64_t *FZ = reinterpret_cast<uint64_t *>(b + c.take((size_t)n * fw * 8));
+  uint64_t *dout = reinterpret_cast<uint64_t *>(b + c.take((size_t)std::max<uint64_t>(1, M) * ow * 8));
+  const bool out_dev = M ? is_device_ptr(record) : true;
+  uint64_t *out = out_dev ? record : dout;
+  QS_CUDA(s, launch_frame_init(FX, FZ, n, (uint32_t)fw, seed, s->stream));
+  s->launches += 1;
+  std::vector<uint32_t> qtmp, seen(n, 0);
+  uint32_t sid = 0;
+  for (const Op &op : s->ops) {
+    if (op.kind == Op::kHostLayer) {
+      int slot;
+      uint8_t *h = ring_slot(s, &slot);
+      if (!h) return cuda_fail(s, cudaGetLastError(), "staging event");
+      memcpy(h, op.packed.data(), op.packed.size() * 4);
+      if ((rc = upload(s, slot, op.packed.size() * 4))) return rc;
+      QS_CUDA(s, launch_frame_layer(FX, FZ, n, (uint32_t)fw, reinterpret_cast<uint32_t *>(s->dstage),
+                                    (uint32_t)(op.packed.size() / 2), s->d.err, s->stream));
+      s->launches += 1;
+    } else if (op.kind == Op::kDevLayers) {
+      for (size_t l = 0; l + 1 < op.ptr.size(); ++l) {
+        const int64_t a = op.ptr[l], cnt = op.ptr[l + 1] - a;
+        QS_CUDA(s, launch_frame_layer(FX, FZ, n, (uint32_t)fw, op.dev + 2 * a, (uint32_t)cnt,
+                                      s->d.err, s->stream));
+        if (cnt) s->launches += 1;
+      }
+    } else {
+      // measurement window: split into runs of distinct qubits (Sec. 5 processes
+      // the measurements of one window in parallel)
+      const uint32_t *qh;
+      uint32_t cnt;
+      if (op.kind == Op::kHostMeasure) {
+        qh = op.qubits.data();
+        cnt = (uint32_t)op.qubits.size();
+      } else {
+        qtmp.resize(op.count);
+        QS_CUDA(s, cudaMemcpyAsync(qtmp.data(), op.dev, (size_t)op.count * 4, cudaMemcpyDeviceToHost,
+                                   s->stream));
+        QS_CUDA(s, cudaStreamSynchronize(s->stream));
+        qh = qtmp.data();
+        cnt = op.count;
+      }
+      const uint32_t chunk = (uint32_t)(s->plan.stage_bytes / 4);
+      uint32_t start = 0;
+      while (start < cnt) {
+        if (++sid == 0) { std::fill(seen.begin(), seen.end(), 0); sid = 1; }
+        uint32_t end = start;
+        while (end < cnt && end - start < chunk && (qh[end] >= n || seen[qh[end]] != sid)) {
+          if (qh[end] < n) seen[qh[end]] = sid;
+          ++end;
+        }
+        int slot;
+        uint8_t *h = ring_slot(s, &slot);
+        if (!h) return cuda_fail(s, cudaGetLastError(), "staging event");
+        memcpy(h, qh + start, (size_t)(end - start) * 4);
+        if ((rc = upload(s, slot, (size_t)(end - start) * 4))) return rc;
+        QS_CUDA(s, launch_frame_measure(FX, FZ, n, (uint32_t)fw,
+                                        reinterpret_cast<uint32_t *>(s->dstage), end - start,
+                                        op.m0 + start, s->d.record, out, shots, seed, s->d.err,
+                                        s->stream));
+        s->launches += (end - start + 65534) / 65535;
+        start = end;
+      }
+    }
+  }
+  if (!out_dev && M)
+    QS_CUDA(s, cudaMemcpyAsync(record, dout, (size_t)(M * ow * 8), cudaMemcpyDeviceToHost, s->stream));
+  if (own) QS_CUDA(s, cudaFreeAsync(ws, s->stream));
+  if (!out_dev) return qs_sim_sync(s);
+  return QS_OK;
+}
+
+int qs_sim_tableau_export(qs_sim *s, int layout, void *dst, size_t dst_bytes, size_t *needed) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (layout != QS_LAYOUT_ROWS_PACKED) return fail(QS_ERR_ARG, "unknown layout");
+  const Layout &L = s->d.L;
+  const uint32_t n = L.n, k = L.k;
+  const size_t sw = (2ull * n + 63) / 64;
+  const size_t bytes = (2ull * n * 2 * k + sw) * 8;
+  if (needed) *needed = bytes;
+  if (!dst) return QS_OK;
+  if (dst_bytes < bytes) return fail(QS_ERR_SIZE, "export buffer too small");
+  if ((rc = ensure_rows(s))) return rc;
+  uint64_t *o = static_cast<uint64_t *>(dst);
+  const size_t dp = 2ull * k * 8, sp = (size_t)L.rs * 8, wb = (size_t)k * 8;
+  QS_CUDA(s, cudaMemcpy2DAsync(o, dp, s->d.RX, sp, wb, n, cudaMemcpyDeviceToHost, s->stream));
+  QS_CUDA(s, cudaMemcpy2DAsync(o + k, dp, s->d.RZ, sp, wb, n, cudaMemcpyDeviceToHost, s->stream));
+  const size_t st = 64ull * k * L.rs;
+  QS_CUDA(s, cudaMemcpy2DAsync(o + (size_t)n * 2 * k, dp, s->d.RX + st, sp, wb, n,
+                               cudaMemcpyDeviceToHost, s->stream));
+  QS_CUDA(s, cudaMemcpy2DAsync(o + (size_t)n * 2 * k + k, dp, s->d.RZ + st, sp, wb, n,
+                               cudaMemcpyDeviceToHost, s->stream));
+  std::vector<uint64_t> S(L.cs);
+  QS_CUDA(s, cudaMemcpyAsync(S.data(), s->d.S, (size_t)L.cs * 8, cudaMemcpyDeviceToHost, s->stream));
+  if ((rc = qs_sim_sync(s))) return rc;
+  uint64_t *sig = o + 2ull * n * 2 * k;
+  for (size_t w = 0; w < sw; ++w) sig[w] = 0;
+  for (uint64_t i = 0; i < 2ull * n; ++i) {
+    const uint64_t pr = i < n ? i : 64ull * k + (i - n);
+    if ((S[pr >> 6] >> (pr & 63)) & 1u) sig[i >> 6] |= 1ull << (i & 63);
+  }
+  return QS_OK;
+}
+
+int qs_sim_export_rows(qs_sim *s, const uint32_t *rows, uint32_t count, uint64_t *dst) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (count && (!rows || !dst)) return fail(QS_ERR_ARG, "NULL argument");
+  const Layout &L = s->d.L;
+  const uint32_t n = L.n, k = L.k;
+  for (uint32_t i = 0; i < count; ++i)
+    if (rows[i] >= 2 * n) return fail(QS_ERR_ARG, "row index >= 2n");
+  if (count == 0) return QS_OK;
+  if ((rc = ensure_rows(s))) return rc;
+  std::vector<uint64_t> S(L.cs);
+  QS_CUDA(s, cudaMemcpyAsync(S.data(), s->d.S, (size_t)L.cs * 8, cudaMemcpyDeviceToHost, s->stream));
+  const size_t per = 2ull * k + 1;
+  for (uint32_t i = 0; i < count; ++i) {
+    const uint64_t pr = rows[i] < n ? rows[i] : 64ull * k + (rows[i] - n);
+    QS_CUDA(s, cudaMemcpyAsync(dst + i * per, s->d.RX + pr * L.rs, (size_t)k * 8,
+                               cudaMemcpyDeviceToHost, s->stream));
+    QS_CUDA(s, cudaMemcpyAsync(dst + i * per + k, s->d.RZ + pr * L.rs, (size_t)k * 8,
+                               cudaMemcpyDeviceToHost, s->stream));
+  }
+  if ((rc = qs_sim_sync(s))) return rc;
+  for (uint32_t i = 0; i < count; ++i) {
+    const uint64_t pr = rows[i] < n ? rows[i] : 64ull * k + (rows[i] - n);
+    dst[i * per + 2 * k] = (S[pr >> 6] >> (pr & 63)) & 1u;
+  }
+  return QS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Layout change between the column-major tableau (gate layers) and the
+// row-major tableau (measurement), Sec. 4.5 (Alg. 4).
+//
+// The paper transposes in place with a shared-memory tile shuffle plus an
+// off-diagonal swap. With 280 GB of HBM the row-major copy lives in its own
+// buffers, so the transpose here is out of place and does one read and one
+// write of each word. One generic kernel serves both directions: it reads a
+// bit matrix M stored as `in` rows of words (bit b of in[i][j] = M[i][64 j + b])
+// and writes M^T the same way.
+//
+// A block is four warps and covers 256 input rows x 4 input words:
+//   - lane l of warp w loads input rows 64 w + l and 64 w + l + 32, 4 words
+//     each (one full 32-byte sector per row);
+//   - each 64 x 64 bit sub-tile is transposed in registers in six
+//     mask/shift rounds: the first between the lane's two rows, the other
+//     five between lanes l and l ^ j with warp shuffles (the bit-group swap
+//     of Alg. 4 with its six masks, done in registers);
+//   - the transposed words meet in shared memory and leave as 32-byte output
+//     row segments.
+#include "qs_internal.cuh"
+
+namespace qs {
+
+__device__ __forceinline__ void transpose64(uint64_t &lo, uint64_t &hi, int lane) {
+  // rows lane (lo) and lane + 32 (hi); after the call lo/hi hold output rows
+  // lane and lane + 32 (bit a of output row b = bit b of input row a).
+  {
+    const uint64_t m = 0x00000000FFFFFFFFull;
+    uint64_t t = ((lo >> 32) ^ hi) & m;
+    lo ^= t << 32;
+    hi ^= t;
+  }
+  const uint64_t masks[5] = {0x0000FFFF0000FFFFull, 0x00FF00FF00FF00FFull, 0x0F0F0F0F0F0F0F0Full,
+                             0x3333333333333333ull, 0x5555555555555555ull};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const uint64_t m = masks[s];
+    uint64_t plo = __shfl_xor_sync(0xffffffffu, lo, j);
+    uint64_t phi = __shfl_xor_sync(0xffffffffu, hi, j);
+    if ((lane & j) == 0) {
+      uint64_t t = ((lo >> j) ^ plo) & m;
+      lo ^= t << j;
+      t = ((hi >> j) ^ phi) & m;
+      hi ^= t << j;
+    } else {
+      uint64_t t = ((plo >> j) ^ lo) & m;
+      lo ^= t;
+      t = ((phi >> j) ^ hi) & m;
+      hi ^= t;
+    }
+  }
+}
+
+// in:  rows_in x words_in (stride in_stride words); out: rows_out x words_out
+// grid.x = words_in / 4, grid.y = rows_in / 256 (both exact by construction)
+__global__ void __launch_bounds__(128)
+bit_transpose_kernel(const uint64_t *__restrict__ in, size_t in_stride, uint64_t *__restrict__ out,
+                     size_t out_stride) {
+  __shared__ uint64_t tile[256][5];  // [output row within block][output word], padded
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t j0 = (size_t)blockIdx.x * 4;        // input word group
+  const size_t i0 = (size_t)blockIdx.y * 256;      // input row group
+  const size_t r0 = i0 + 64 * warp + lane;
+  const ulonglong2 *p0 = reinterpret_cast<const ulonglong2 *>(in + r0 * in_stride + j0);
+  const ulonglong2 *p1 = reinterpret_cast<const ulonglong2 *>(in + (r0 + 32) * in_stride + j0);
+  ulonglong2 a0 = p0[0], a1 = p0[1], b0 = p1[0], b1 = p1[1];
+  uint64_t lo[4] = {a0.x, a0.y, a1.x, a1.y};
+  uint64_t hi[4] = {b0.x, b0.y, b1.x, b1.y};
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    transpose64(lo[s], hi[s], lane);
+    // sub-tile (input word j0 + s, input rows i0 + 64 warp ..): output rows
+    // 64 (j0 + s) + b, output word i0 / 64 + warp
+    tile[64 * s + lane][warp] = lo[s];
+    tile[64 * s + lane + 32][warp] = hi[s];
+  }
+  __syncthreads();
+  // 256 output rows x 4 words: thread t writes rows t and t + 128
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int rr = threadIdx.x + 128 * h;
+    const size_t orow = 64 * j0 + rr;
+    ulonglong2 *q = reinterpret_cast<ulonglong2 *>(out + orow * out_stride + i0 / 64);
+    q[0] = make_ulonglong2(tile[rr][0], tile[rr][1]);
+    q[1] = make_ulonglong2(tile[rr][2], tile[rr][3]);
+  }
+}
+
+cudaError_t launch_to_rows(const Dev &d, cudaStream_t s) {
+  // in = X/Z: rows = ncols (qubits), words = cs; out = RX/RZ: rows = 64 cs, words = rs
+  const Layout &L = d.L;
+  dim3 grid(L.cs / 4, L.ncols / 256);
+  bit_transpose_kernel<<<grid, 128, 0, s>>>(d.X, L.cs, d.RX, L.rs);
+  bit_transpose_kernel<<<grid, 128, 0, s>>>(d.Z, L.cs, d.RZ, L.rs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_cols(const Dev &d, cudaStream_t s) {
+  // in = RX/RZ: rows = 64 cs, words = rs; out = X/Z: rows = 64 rs = ncols, words = cs
+  const Layout &L = d.L;
+  dim3 grid(L.rs / 4, (unsigned)(L.nrows / 256));
+  bit_transpose_kernel<<<grid, 128, 0, s>>>(d.RX, L.rs, d.X, L.cs);
+  bit_transpose_kernel<<<grid, 128, 0, s>>>(d.RZ, L.rs, d.Z, L.cs);
+  return cudaGetLastError();
+}
+
+}  // namespace qs

@@ -1,0 +1,353 @@
+"""Thin Python binding of libqs (include/qs.h): argument marshalling only.
+
+Every step of the simulation runs in the CUDA library. The module-level
+functions carry the C names; `Simulator` bundles them with PyTorch, which only
+provides device memory (the sim workspace, device-resident circuits, frame
+buffers) and the CUDA stream. There is no CPU fallback: if libqs.so cannot be
+built or loaded, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+QS_OK = 0
+ERRORS = {-1: "QS_ERR_ARG", -2: "QS_ERR_OOM", -3: "QS_ERR_CUDA", -4: "QS_ERR_TIMEOUT",
+          -5: "QS_ERR_SIZE", -6: "QS_ERR_STATE", -7: "QS_ERR_INTERNAL"}
+QS_LAYOUT_ROWS_PACKED = 0
+
+GATES = dict(I=0, X=1, Y=2, Z=3, H=4, S=5, SDG=6, CX=7, CY=8, CZ=9, SWAP=10, ISWAP=11)
+
+
+class QsError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class qs_key(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("shot", ctypes.c_uint64)]
+
+
+class qs_options(ctypes.Structure):
+    _fields_ = [("record_capacity", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class qs_gate(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_uint32), ("q0", ctypes.c_uint32), ("q1", ctypes.c_uint32)]
+
+
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_sz = ctypes.c_size_t
+
+# name -> (restype, argtypes); the exported C-ABI of libqs
+SIGNATURES = {
+    "qs_version": (ctypes.c_char_p, []),
+    "qs_last_error": (ctypes.c_char_p, []),
+    "qs_sim_required_bytes": (_sz, [_u32, _vp]),
+    "qs_sim_create": (ctypes.c_int, [_u32, _vp, _vp, _vp, _sz, ctypes.POINTER(_vp)]),
+    "qs_sim_destroy": (ctypes.c_int, [_vp]),
+    "qs_sim_reset": (ctypes.c_int, [_vp, _vp]),
+    "qs_sim_apply_layer": (ctypes.c_int, [_vp, _vp, _u32]),
+    "qs_pack_layers": (ctypes.c_int, [_u32, _vp, _vp, _u32, _vp]),
+    "qs_sim_apply_layers_dev": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32]),
+    "qs_sim_measure": (ctypes.c_int, [_vp, _vp, _u32, qs_key, _vp]),
+    "qs_sim_measure_dev": (ctypes.c_int, [_vp, _vp, _u32, qs_key]),
+    "qs_sim_num_measurements": (_u64, [_vp]),
+    "qs_sim_record": (ctypes.c_int, [_vp, _u64, _u64, _vp]),
+    "qs_sim_sample_required_bytes": (_sz, [_vp, _u64]),
+    "qs_sim_sample": (ctypes.c_int, [_vp, _u64, _u64, _vp, _sz, _vp, _sz]),
+    "qs_sim_tableau_export": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _sz, ctypes.POINTER(_sz)]),
+    "qs_sim_export_rows": (ctypes.c_int, [_vp, _vp, _u32, _vp]),
+    "qs_sim_sync": (ctypes.c_int, [_vp]),
+    "qs_sim_launch_count": (_u64, [_vp]),
+}
+
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Loads libqs.so (building it in-tree first if needed); raises if it cannot."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError(f"libqs.so not found at {path}; run paper_2603_14641_gb300/build.py")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != QS_OK:
+        raise QsError(rc, where, lib().qs_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# ----------------------------------------------------------------------
+# Module-level functions with the C names (argument marshalling only)
+# ----------------------------------------------------------------------
+
+def qs_version() -> str:
+    return lib().qs_version().decode()
+
+
+def qs_sim_required_bytes(n: int, record_capacity: int = 0) -> int:
+    opt = qs_options(record_capacity, 0, 0)
+    return int(lib().qs_sim_required_bytes(n, ctypes.byref(opt)))
+
+
+def qs_sim_create(n: int, stream: int = 0, workspace: int = 0, workspace_bytes: int = 0,
+                  record_capacity: int = 0) -> int:
+    opt = qs_options(record_capacity, 0, 0)
+    h = ctypes.c_void_p()
+    _check(lib().qs_sim_create(n, ctypes.byref(opt), ctypes.c_void_p(stream or None),
+                               ctypes.c_void_p(workspace or None), workspace_bytes,
+                               ctypes.byref(h)), "qs_sim_create")
+    return h.value
+
+
+def qs_sim_destroy(sim: int) -> None:
+    _check(lib().qs_sim_destroy(ctypes.c_void_p(sim)), "qs_sim_destroy")
+
+
+def qs_sim_reset(sim: int, initstate: Optional[np.ndarray] = None) -> None:
+    a = None if initstate is None else np.ascontiguousarray(initstate, np.uint8)
+    _check(lib().qs_sim_reset(ctypes.c_void_p(sim), None if a is None else _ptr(a)), "qs_sim_reset")
+
+
+def _as_gates(gates: np.ndarray) -> np.ndarray:
+    g = np.ascontiguousarray(np.asarray(gates, dtype=np.uint32).reshape(-1, 3))
+    return g
+
+
+def qs_sim_apply_layer(sim: int, gates: np.ndarray) -> None:
+    g = _as_gates(gates)
+    _check(lib().qs_sim_apply_layer(ctypes.c_void_p(sim), _ptr(g), g.shape[0]), "qs_sim_apply_layer")
+
+
+def qs_pack_layers(n: int, gates: np.ndarray, layer_ptr: np.ndarray) -> np.ndarray:
+    g = _as_gates(gates)
+    lp = np.ascontiguousarray(layer_ptr, np.int64)
+    out = np.zeros(2 * max(int(lp[-1]), 1), np.uint32)
+    _check(lib().qs_pack_layers(n, _ptr(g) if g.size else None, _ptr(lp), len(lp) - 1, _ptr(out)),
+           "qs_pack_layers")
+    return out[:2 * int(lp[-1])]
+
+
+def qs_sim_apply_layers_dev(sim: int, packed_dev: int, layer_ptr: np.ndarray, l_begin: int,
+                            l_end: int) -> None:
+    lp = np.ascontiguousarray(layer_ptr, np.int64)
+    _check(lib().qs_sim_apply_layers_dev(ctypes.c_void_p(sim), ctypes.c_void_p(packed_dev),
+                                         _ptr(lp), l_begin, l_end), "qs_sim_apply_layers_dev")
+
+
+def qs_sim_measure(sim: int, qubits: np.ndarray, seed: int, shot: int = 0,
+                   want_outcomes: bool = True) -> Optional[np.ndarray]:
+    q = np.ascontiguousarray(qubits, np.uint32)
+    out = np.zeros(len(q), np.uint8) if want_outcomes else None
+    _check(lib().qs_sim_measure(ctypes.c_void_p(sim), _ptr(q) if len(q) else None, len(q),
+                                qs_key(seed, shot), _ptr(out) if (want_outcomes and len(q)) else None),
+           "qs_sim_measure")
+    return out
+
+
+def qs_sim_measure_dev(sim: int, qubits_dev: int, count: int, seed: int, shot: int = 0) -> None:
+    _check(lib().qs_sim_measure_dev(ctypes.c_void_p(sim), ctypes.c_void_p(qubits_dev), count,
+                                    qs_key(seed, shot)), "qs_sim_measure_dev")
+
+
+def qs_sim_num_measurements(sim: int) -> int:
+    return int(lib().qs_sim_num_measurements(ctypes.c_void_p(sim)))
+
+
+def qs_sim_record(sim: int, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+    if count is None:
+        count = qs_sim_num_measurements(sim) - first
+    out = np.zeros(max(count, 1), np.uint8)
+    _check(lib().qs_sim_record(ctypes.c_void_p(sim), first, count, _ptr(out)), "qs_sim_record")
+    return out[:count]
+
+
+def qs_sim_sample_required_bytes(sim: int, shots: int) -> int:
+    return int(lib().qs_sim_sample_required_bytes(ctypes.c_void_p(sim), shots))
+
+
+def qs_sim_sample(sim: int, shots: int, seed: int, record: int, record_words: int,
+                  frame_ws: int = 0, frame_ws_bytes: int = 0) -> None:
+    _check(lib().qs_sim_sample(ctypes.c_void_p(sim), shots, seed, ctypes.c_void_p(record or None),
+                               record_words, ctypes.c_void_p(frame_ws or None), frame_ws_bytes),
+           "qs_sim_sample")
+
+
+def qs_sim_tableau_export(sim: int) -> np.ndarray:
+    need = ctypes.c_size_t(0)
+    _check(lib().qs_sim_tableau_export(ctypes.c_void_p(sim), QS_LAYOUT_ROWS_PACKED, None, 0,
+                                       ctypes.byref(need)), "qs_sim_tableau_export")
+    buf = np.zeros(need.value // 8, np.uint64)
+    _check(lib().qs_sim_tableau_export(ctypes.c_void_p(sim), QS_LAYOUT_ROWS_PACKED, _ptr(buf),
+                                       need.value, None), "qs_sim_tableau_export")
+    return buf
+
+
+def qs_sim_export_rows(sim: int, rows: np.ndarray, n: int):
+    """Selected generator rows -> (x, z, r) uint8 arrays of shapes (R, n), (R, n), (R,)."""
+    r = np.ascontiguousarray(rows, np.uint32)
+    k = (n + 63) // 64
+    buf = np.zeros((max(len(r), 1), 2 * k + 1), np.uint64)
+    _check(lib().qs_sim_export_rows(ctypes.c_void_p(sim), _ptr(r) if len(r) else None, len(r),
+                                    _ptr(buf)), "qs_sim_export_rows")
+    buf = buf[:len(r)]
+    bits = np.unpackbits(np.ascontiguousarray(buf[:, :2 * k]).view(np.uint8).reshape(len(r), -1),
+                         axis=1, bitorder="little")
+    x = np.ascontiguousarray(bits[:, :n])
+    z = np.ascontiguousarray(bits[:, 64 * k:64 * k + n])
+    return x, z, (buf[:, 2 * k] & 1).astype(np.uint8)
+
+
+def qs_sim_sync(sim: int) -> None:
+    _check(lib().qs_sim_sync(ctypes.c_void_p(sim)), "qs_sim_sync")
+
+
+def qs_sim_launch_count(sim: int) -> int:
+    return int(lib().qs_sim_launch_count(ctypes.c_void_p(sim)))
+
+
+def unpack_rows(buf: np.ndarray, n: int):
+    """ROWS_PACKED export -> (x, z, r) uint8 arrays of shapes (2n, n), (2n, n), (2n,)."""
+    k = (n + 63) // 64
+    rows = buf[:2 * n * 2 * k].reshape(2 * n, 2 * k)
+    bits = np.unpackbits(rows.view(np.uint8).reshape(2 * n, 2 * k, 8)[..., :], axis=2,
+                         bitorder="little").reshape(2 * n, 2 * k * 64)
+    x = bits[:, :n]
+    z = bits[:, k * 64:k * 64 + n]
+    sw = (2 * n + 63) // 64
+    sig = np.unpackbits(buf[2 * n * 2 * k:2 * n * 2 * k + sw].view(np.uint8), bitorder="little")
+    return np.ascontiguousarray(x), np.ascontiguousarray(z), np.ascontiguousarray(sig[:2 * n])
+
+
+# ----------------------------------------------------------------------
+# Convenience wrapper (PyTorch supplies device memory and the stream)
+# ----------------------------------------------------------------------
+
+@dataclass
+class DeviceCircuit:
+    """A circuit's gate layers packed and resident in device memory."""
+    n: int
+    packed: "object"        # torch.uint32-compatible int32 device tensor
+    layer_ptr: np.ndarray   # int64 host offsets
+    n_gates: int
+
+
+class Simulator:
+    def __init__(self, n: int, device: str = "cuda", stream=None, record_capacity: int = 0):
+        import torch
+        self.torch = torch
+        self.n = int(n)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = qs_sim_required_bytes(self.n, record_capacity)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.sim = qs_sim_create(self.n, self.stream.cuda_stream, self.workspace.data_ptr(), nbytes,
+                                 record_capacity)
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "sim", None):
+            qs_sim_destroy(self.sim)
+            self.sim = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, initstate=None):
+        self._keep.clear()
+        qs_sim_reset(self.sim, initstate)
+
+    def apply_layer(self, gates):
+        qs_sim_apply_layer(self.sim, gates)
+
+    def upload(self, circuit) -> DeviceCircuit:
+        packed = qs_pack_layers(circuit.n, circuit.gates, circuit.layer_ptr)
+        t = self.torch.from_numpy(packed.view(np.int32)).to(self.device)
+        return DeviceCircuit(circuit.n, t, np.asarray(circuit.layer_ptr, np.int64), circuit.n_gates)
+
+    def apply_layers_dev(self, dc: DeviceCircuit, l0: int, l1: int):
+        self._keep.append(dc.packed)
+        qs_sim_apply_layers_dev(self.sim, dc.packed.data_ptr(), dc.layer_ptr, l0, l1)
+
+    def measure(self, qubits, seed: int, shot: int = 0, want_outcomes: bool = True):
+        return qs_sim_measure(self.sim, qubits, seed, shot, want_outcomes)
+
+    def measure_dev(self, qubits_dev, seed: int, shot: int = 0):
+        self._keep.append(qubits_dev)
+        qs_sim_measure_dev(self.sim, qubits_dev.data_ptr(), qubits_dev.numel(), seed, shot)
+
+    def run(self, circuit, seed: int, shot: int = 0, dc: Optional[DeviceCircuit] = None):
+        """Runs circuit.ops; layers from host (or from `dc` if given). Returns the record."""
+        for op in circuit.ops:
+            if op[0] == "layers":
+                if dc is not None:
+                    self.apply_layers_dev(dc, op[1], op[2])
+                else:
+                    for l in range(op[1], op[2]):
+                        self.apply_layer(circuit.layer(l))
+            else:
+                self.measure(op[1], seed, shot, want_outcomes=False)
+        return self.record()
+
+    @property
+    def num_measurements(self) -> int:
+        return qs_sim_num_measurements(self.sim)
+
+    def record(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        return qs_sim_record(self.sim, first, count)
+
+    def export(self):
+        return unpack_rows(qs_sim_tableau_export(self.sim), self.n)
+
+    def sample(self, shots: int, seed: int, on_device: bool = True):
+        """Frame samples; returns (M, ceil(shots/64)) uint64 words (torch on device
+        or numpy on host)."""
+        M = self.num_measurements
+        ow = (shots + 63) // 64
+        fb = qs_sim_sample_required_bytes(self.sim, shots)
+        fws = self.torch.empty(fb, dtype=self.torch.uint8, device=self.device)
+        if on_device:
+            out = self.torch.zeros((max(M, 1), ow), dtype=self.torch.int64, device=self.device)
+            qs_sim_sample(self.sim, shots, seed, out.data_ptr(), M * ow, fws.data_ptr(), fb)
+            return out[:M]
+        out = np.zeros((max(M, 1), ow), np.uint64)
+        qs_sim_sample(self.sim, shots, seed, out.ctypes.data, M * ow, fws.data_ptr(), fb)
+        return out[:M]
+
+    def export_rows(self, rows):
+        return qs_sim_export_rows(self.sim, rows, self.n)
+
+    def sync(self):
+        qs_sim_sync(self.sim)
+
+    @property
+    def launch_count(self) -> int:
+        return qs_sim_launch_count(self.sim)

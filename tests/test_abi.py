@@ -1,0 +1,94 @@
+"""Host-side checks of the C ABI (no GPU): the library builds and loads, every
+function declared in include/qs.h is exported, the gate codes agree with the
+input format, and host validation rejects bad layers."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2603_14641_gb300 import qs
+from workloads import circuits as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qs.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qs_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for want in ["qs_sim_create", "qs_sim_destroy", "qs_sim_apply_layer", "qs_sim_measure",
+                 "qs_sim_sample", "qs_sim_tableau_export"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = qs.lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", L._name], capture_output=True, text=True)
+    exported = set(re.findall(r"\bT\s+(qs_[a-z_0-9]+)$", out.stdout, flags=re.M))
+    missing = [f for f in _declared_functions() if f not in exported]
+    assert not missing, missing
+    for f in _declared_functions():
+        assert f in qs.SIGNATURES, f"binding lacks {f}"
+
+
+def test_gate_codes_match_input_format():
+    text = open(HEADER).read()
+    for name in C.GATE_NAMES:
+        m = re.search(rf"QS_{name}\s*=\s*(\d+)", text)
+        assert m, name
+        assert int(m.group(1)) == getattr(C, name) == qs.GATES[name]
+
+
+def test_version_and_required_bytes():
+    assert "sm_103a" in qs.qs_version()
+    n = 180_000
+    b = qs.qs_sim_required_bytes(n)
+    k = (n + 63) // 64
+    cs = (2 * k + 3) // 4 * 4
+    ncols = (n + 255) // 256 * 256
+    # column-major X, Z and row-major RX, RZ dominate: ~n^2 bytes in total
+    assert b >= 2 * ncols * cs * 8 + 2 * (64 * cs) * (ncols // 64) * 8
+    assert b < 1.02 * n * n + (1 << 28)
+    assert qs.qs_sim_required_bytes(0) == 0
+
+
+def test_pack_layers_format_and_validation():
+    circ = C.random_circuit(100, 5, 0.5, seed=3)
+    packed = qs.qs_pack_layers(circ.n, circ.gates, circ.layer_ptr)
+    g = circ.gates
+    assert np.array_equal(packed[0::2], (g[:, 0] << 24) | g[:, 1])
+    two = np.isin(g[:, 0], C.TWO_QUBIT)
+    assert np.array_equal(packed[1::2], np.where(two, g[:, 2], 0))
+    bad = [
+        np.array([[C.CX, 1, 1]], np.uint32),            # two-qubit gate on one qubit
+        np.array([[C.H, 3, 0], [C.S, 3, 0]], np.uint32),  # qubit used twice in a layer
+        np.array([[C.H, 100, 0]], np.uint32),           # qubit out of range
+        np.array([[12, 0, 0]], np.uint32),              # unknown gate type
+        np.array([[C.CZ, 5, 100]], np.uint32),          # target out of range
+    ]
+    for b in bad:
+        with pytest.raises(qs.QsError) as e:
+            qs.qs_pack_layers(100, b, np.array([0, len(b)]))
+        assert e.value.code == -1
+    # the same qubit in two different layers is fine
+    ok = np.array([[C.H, 3, 0], [C.S, 3, 0]], np.uint32)
+    qs.qs_pack_layers(100, ok, np.array([0, 1, 2]))
+
+
+def test_create_without_device_fails_loudly():
+    """Without a usable GPU the product path raises instead of falling back."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    with pytest.raises(qs.QsError):
+        qs.qs_sim_create(64)

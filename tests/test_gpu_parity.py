@@ -1,0 +1,269 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+bit-exact on tableau bits, signs, measurement records and frame samples.
+
+Sizes the oracle finishes in seconds cover several 64-bit words, several
+256x256 transpose tiles and ragged tails; at the full workload sizes (10,000
+and 180,000 qubits) the checks use sampled rows the oracle can follow alone
+(gate rules act row by row) and properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2603_14641_gb300 import qs  # noqa: E402
+from workloads import circuits as C  # noqa: E402
+
+
+def _sim(n, **kw):
+    return qs.Simulator(n, device="cuda:0", **kw)
+
+
+def _assert_tableau(sim, o):
+    x, z, r = sim.export()
+    ox, oz, orr = o.get()
+    assert np.array_equal(x, ox), "x bits differ"
+    assert np.array_equal(z, oz), "z bits differ"
+    assert np.array_equal(r, orr), "signs differ"
+
+
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 127, 256, 300, 1000, 2000])
+def test_gate_layers_bit_exact(n):
+    circ = C.gate_mix_circuit(n, 16, seed=n, final_measure_all=False)
+    sim = _sim(n)
+    sim.run(circ, seed=1)
+    o, _, _ = O.run_circuit(circ, seed=1)
+    _assert_tableau(sim, o)
+    sim.sync()
+
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (3, 2), (64, 3), (65, 4), (300, 5), (700, 6), (2000, 7)])
+def test_measurements_bit_exact(n, seed):
+    circ = C.gate_mix_circuit(n, 24, seed=seed, measure_every=5, measure_frac=0.3)
+    sim = _sim(n)
+    rec = sim.run(circ, seed=seed * 13, shot=seed)
+    o, orec, kinds = O.run_circuit(circ, seed=seed * 13, shot=seed)
+    assert np.array_equal(rec, orec), "records differ"
+    _assert_tableau(sim, o)
+    sim.sync()
+
+
+def test_workload_256_full():
+    """n = 256, depth 100, final measurement of all qubits, 1 shot."""
+    circ = C.workload_256()
+    sim = _sim(circ.n)
+    rec = sim.run(circ, seed=2026)
+    o, orec, kinds = O.run_circuit(circ, seed=2026)
+    assert np.array_equal(rec, orec)
+    assert kinds.sum() > 0 and (kinds == 0).sum() > 0  # both measurement kinds occur
+    _assert_tableau(sim, o)
+    sim.sync()
+
+
+def test_hsc_generator_with_periodic_measurements():
+    """Same generator as the 10,000-qubit workload, at n = 2000 (5% every 10 layers)."""
+    circ = C.random_circuit(2000, 40, 0.5, seed=2, measure_every=10, measure_frac=0.05)
+    sim = _sim(circ.n)
+    rec = sim.run(circ, seed=99)
+    o, orec, _ = O.run_circuit(circ, seed=99)
+    assert np.array_equal(rec, orec)
+    _assert_tableau(sim, o)
+
+
+def test_repeated_and_deterministic_measurements():
+    n = 150
+    circ = C.gate_mix_circuit(n, 10, seed=4, final_measure_all=False)
+    qubits = np.array([3, 3, 77, 149, 0, 77, 3, 149, 0], np.uint32)
+    sim = _sim(n)
+    sim.run(circ, seed=1)
+    out = sim.measure(qubits, seed=5, shot=2)
+    o, _, _ = O.run_circuit(circ, seed=1)
+    oout, kinds = o.measure(qubits, seed=5, shot=2)
+    assert np.array_equal(out, oout)
+    assert kinds[1] == 0 and out[1] == out[0]
+    _assert_tableau(sim, o)
+
+
+def test_ghz_closed_form_on_gpu():
+    n = 1000
+    g = [[C.H, 0, 0]]
+    sim = _sim(n)
+    sim.apply_layer(np.array(g, np.uint32))
+    for i in range(1, n):
+        sim.apply_layer(np.array([[C.CX, i - 1, i]], np.uint32))
+    out = sim.measure(np.arange(n), seed=8, shot=1)
+    assert (out == out[0]).all() and out[0] == O.coin(8, 1, 0)
+    sim.sync()
+
+
+def test_initstate_reset():
+    n = 70
+    init = (np.arange(n) % 3 == 0).astype(np.uint8)
+    sim = _sim(n)
+    sim.reset(init)
+    out = sim.measure(np.arange(n), seed=0)
+    assert np.array_equal(out, init)
+    o = O.Oracle(n)
+    o.reset(init)
+    o.measure(np.arange(n), seed=0)
+    _assert_tableau(sim, o)
+
+
+def test_device_resident_layers_match_host_path():
+    circ = C.gate_mix_circuit(500, 20, seed=9, measure_every=7, measure_frac=0.2)
+    a = _sim(circ.n)
+    ra = a.run(circ, seed=3)
+    b = _sim(circ.n)
+    dc = b.upload(circ)
+    rb = b.run(circ, seed=3, dc=dc)
+    assert np.array_equal(ra, rb)
+    xa, za, sa = a.export()
+    xb, zb, sb = b.export()
+    assert np.array_equal(xa, xb) and np.array_equal(za, zb) and np.array_equal(sa, sb)
+
+
+def test_device_qubit_list_matches_host_list():
+    circ = C.random_circuit(300, 12, 0.5, seed=5, final_measure_all=False)
+    q = np.array([5, 17, 17, 299, 0, 128], np.uint32)
+    a = _sim(circ.n)
+    a.run(circ, seed=0)
+    ra = a.measure(q, seed=4)
+    b = _sim(circ.n)
+    b.run(circ, seed=0)
+    b.measure_dev(torch.from_numpy(q.view(np.int32)).cuda(), seed=4)
+    assert np.array_equal(ra, b.record())
+
+
+def test_run_twice_is_identical():
+    """XOR atomics are order independent: two runs agree bit for bit."""
+    circ = C.random_circuit(3000, 30, 0.5, seed=6, measure_every=10, measure_frac=0.05)
+    outs = []
+    for _ in range(2):
+        s = _sim(circ.n)
+        rec = s.run(circ, seed=17)
+        outs.append((rec, s.export()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for a, b in zip(outs[0][1], outs[1][1]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("n,shots", [(5, 1), (64, 64), (300, 200), (130, 1000)])
+def test_frames_bit_exact(n, shots):
+    circ = C.gate_mix_circuit(n, 18, seed=n + shots, measure_every=4, measure_frac=0.4)
+    sim = _sim(n)
+    rec = sim.run(circ, seed=21)
+    words = sim.sample(shots, seed=33, on_device=False)
+    bits = np.unpackbits(words.view(np.uint8), axis=1, bitorder="little")
+    assert not bits[:, shots:].any()  # tail bits beyond `shots` are zero
+    ref = O.frames(circ, rec, shots, seed=33)
+    assert np.array_equal(bits[:, :shots], ref)
+    words_dev = sim.sample(shots, seed=33, on_device=True).cpu().numpy().view(np.uint64)
+    assert np.array_equal(words_dev, words)
+
+
+def test_frames_device_resident_replay():
+    circ = C.random_circuit(400, 20, 0.5, seed=8, measure_every=5, measure_frac=0.1)
+    sim = _sim(circ.n)
+    dc = sim.upload(circ)
+    rec = sim.run(circ, seed=2, dc=dc)
+    shots = 333
+    words = sim.sample(shots, seed=4, on_device=False)
+    bits = np.unpackbits(words.view(np.uint8), axis=1, bitorder="little")[:, :shots]
+    assert np.array_equal(bits, O.frames(circ, rec, shots, seed=4))
+
+
+def test_errors_are_reported():
+    sim = _sim(10, record_capacity=4)
+    with pytest.raises(qs.QsError) as e:
+        sim.measure(np.array([10], np.uint32), seed=0)
+    assert e.value.code == -1
+    with pytest.raises(qs.QsError) as e:
+        sim.apply_layer(np.array([[C.H, 2, 0], [C.CX, 2, 3]], np.uint32))
+    assert e.value.code == -1
+    with pytest.raises(qs.QsError) as e:
+        sim.measure(np.arange(5, dtype=np.uint32), seed=0)
+    assert e.value.code == -5
+    sim.measure(np.arange(4, dtype=np.uint32), seed=0)  # the sim is still usable
+    sim.sync()
+
+
+# ----------------------------------------------------------------------
+# Full sizes: sampled rows and properties that hold at any size
+# ----------------------------------------------------------------------
+
+def _row_subset_check(circ, layers, nrows, seed):
+    rng = np.random.default_rng(seed)
+    n = circ.n
+    rows = np.sort(rng.choice(2 * n, size=nrows, replace=False)).astype(np.uint32)
+    sim = _sim(n)
+    dc = sim.upload(circ)
+    sim.apply_layers_dev(dc, 0, layers)
+    gx, gz, gr = sim.export_rows(rows)
+    sub = O.RowSubset(n, rows)
+    sub.apply(circ.gates[:circ.layer_ptr[layers]])
+    ox, oz, orr = sub.get()
+    assert np.array_equal(gx, ox) and np.array_equal(gz, oz) and np.array_equal(gr, orr)
+    return sim
+
+
+def test_row_subset_parity_10k():
+    circ = C.workload_10k()
+    sim = _row_subset_check(circ, 50, 48, seed=1)
+    sim.sync()
+
+
+def test_full_10k_measurement_properties():
+    """10,000 qubits: 50 layers, one 5% round, then the same qubits again
+    (all deterministic, same outcomes)."""
+    circ = C.workload_10k()
+    sim = _sim(circ.n)
+    dc = sim.upload(circ)
+    sim.apply_layers_dev(dc, 0, 50)
+    q = circ.ops[1][1]
+    first = sim.measure(q, seed=7)
+    again = sim.measure(q, seed=7)
+    assert np.array_equal(first, again)
+    sim.sync()
+
+
+@pytest.mark.slow
+def test_row_subset_parity_180k():
+    circ = C.workload_180k(depth=6)
+    sim = _row_subset_check(circ, 6, 24, seed=2)
+    sim.sync()
+
+
+@pytest.mark.slow
+def test_full_180k_measure_twice_and_inverse():
+    """180,000 qubits: measurements repeated give the same outcomes; a circuit
+    followed by its inverse restores the initial rows exactly."""
+    n = 180_000
+    circ = C.workload_180k(depth=4)
+    sim = _sim(n)
+    dc = sim.upload(circ)
+    sim.apply_layers_dev(dc, 0, 4)
+    q = np.array([0, 1, 89_999, 179_999], np.uint32)
+    first = sim.measure(q, seed=3)
+    again = sim.measure(q, seed=3)
+    assert np.array_equal(first, again)
+    # inverse check on a fresh sim: layers then their inverses (H, S^dag, CX)
+    inv = {C.H: C.H, C.S: C.SDG, C.CX: C.CX}
+    sim2 = _sim(n)
+    sim2.apply_layers_dev(dc, 0, 4)
+    for l in reversed(range(4)):
+        g = circ.layer(l).copy()
+        g[:, 0] = [inv[int(t)] for t in g[:, 0]]
+        sim2.apply_layer(g)
+    rows = np.array([0, 5, 179_999, 180_000, 250_000, 359_999], np.uint32)
+    x, z, r = sim2.export_rows(rows)
+    for i, row in enumerate(rows):
+        want_x = np.zeros(n, np.uint8)
+        want_z = np.zeros(n, np.uint8)
+        if row < n:
+            want_x[row] = 1
+        else:
+            want_z[row - n] = 1
+        assert np.array_equal(x[i], want_x) and np.array_equal(z[i], want_z) and r[i] == 0
+    sim2.sync()
