@@ -1,0 +1,468 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 stabilizer simulator on the 180,000-qubit workload.
+
+Workload (synthetic, seeded; stands in for the paper's Qiskit heavy suite):
+  180,000 qubits, 1,000 random Clifford layers (CX probability 0.4, seed 3),
+  final Z-measurement of all qubits.
+One step = one pass of the whole hot path on that circuit:
+  tableau init + all 1,000 gate layers (device-resident gate records)
+  + layout switch + the first M of the 180,000 final Z-measurements
+  + F-shot Pauli-frame sampling of those ops (frames through all 1,000
+    layers and the M measurements).
+The full final measurement (180,000 sequential measurements, ~10^15 bytes of
+row traffic) does not fit a bounded step; its first M measurements are the
+most expensive ones (densest tableau) and are timed as the measurement phase.
+
+value = Clifford gates applied / device time of the timed steps (CUDA events on
+the sim's stream, max over ranks); the JSON line also gives per-phase rates
+(gate-phase gates/s, measurements/s, shots/s), the roofline of the gate-layer
+kernel, an end-to-end run through the host-buffer C-ABI calls and the oracle
+timed on the host cores.
+
+--impl reference times the CPU oracle (chp_oracle.c) as it stands on the
+host cores for the same metric, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import circuits as C  # noqa: E402
+
+METRIC = "Clifford gates/s and measurements/s at 180k qubits; shots/s; % of HBM roofline"
+N_QUBITS = 180_000
+DEPTH = 1_000
+FALLBACK_HBM_GBS = 6800.0
+
+# ncu DRAM traffic of one gate-layer launch on the 180k workload, and the hash
+# of the kernel source it was taken with (null once the kernel changes).
+GATE_KERNEL_TRAFFIC = {"bytes_per_launch": None, "source_sha256": None}
+
+
+def _kernel_hash() -> str:
+    p = os.path.join(ROOT, "paper_2603_14641_gb300", "csrc", "qs_gates.cu")
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------
+# distributed helpers (replicas: one independent circuit per GPU)
+# ----------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(value: float, ws: int, backend_device=None) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=backend_device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, ws: int, backend_device=None) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=backend_device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------
+# algorithmic bytes of one gate layer (columns of 2n bits = n/4 bytes)
+# ----------------------------------------------------------------------
+COLS_TOUCHED = {C.H: 4, C.S: 3, C.SDG: 3, C.CX: 6, C.CZ: 6, C.CY: 6, C.SWAP: 8, C.ISWAP: 8,
+                C.X: 1, C.Z: 1, C.Y: 2}
+
+
+def layer_bytes(gates: np.ndarray, n: int) -> float:
+    cols = sum(COLS_TOUCHED[int(t)] * int(c) for t, c in zip(*np.unique(gates[:, 0],
+                                                                           return_counts=True)))
+    return cols * (n / 4.0) + n / 2.0  # + signs: read and write 2n bits
+
+
+# ----------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_2603_14641_gb300 import qs
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    t_gen = time.time()
+    circ = C.random_circuit(args.n, args.depth, 0.4, seed=3, name="n180k_d1000")
+    gen_s = time.time() - t_gen
+    n, L = circ.n, circ.n_layers
+    M, shots = args.measurements, args.shots
+    seed = 1234 + rank
+
+    stream = torch.cuda.Stream(device=dev)
+    sim = qs.Simulator(n, device=str(dev), stream=stream)
+    packed_host = qs.qs_pack_layers(n, circ.gates, circ.layer_ptr)
+    packed_dev = torch.from_numpy(packed_host.view(np.int32)).to(dev)
+    lp = np.asarray(circ.layer_ptr, np.int64)
+    qubits = np.arange(M, dtype=np.uint32)  # the final measurement goes in ascending order
+    q_dev = torch.from_numpy(qubits.view(np.int32)).to(dev)
+    ow = (shots + 63) // 64
+    rec_dev = torch.zeros((M, ow), dtype=torch.int64, device=dev)
+    # frame workspace for the step's op log (sim op log holds L layers + M measurements)
+    fw_bytes = 2 * n * ((ow + 3) // 4 * 4) * 8 + max(M, 1) * ow * 8 + 4096
+    fws = torch.empty(fw_bytes, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def step(ev):
+        qs.qs_sim_reset(sim.sim, None)
+        ev[0].record(stream)
+        qs.qs_sim_apply_layers_dev(sim.sim, packed_dev.data_ptr(), lp, 0, L)
+        ev[1].record(stream)
+        qs.qs_sim_measure_dev(sim.sim, q_dev.data_ptr(), M, seed, 0)
+        ev[2].record(stream)
+        qs.qs_sim_sample(sim.sim, shots, seed + 7, rec_dev.data_ptr(), M * ow, fws.data_ptr(),
+                         fw_bytes)
+        ev[3].record(stream)
+
+    def mk():
+        return [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    for _ in range(args.warmup):
+        step(mk())
+    qs.qs_sim_sync(sim.sim)
+    torch.cuda.synchronize()
+
+    evs = [mk() for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = qs.qs_sim_launch_count(sim.sim)
+    with ClockSampler(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    launches = qs.qs_sim_launch_count(sim.sim) - launches0
+    qs.qs_sim_sync(sim.sim)  # device self-checks
+    total_ms = start.elapsed_time(end)
+    gate_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
+    meas_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
+    samp_ms = sum(e[2].elapsed_time(e[3]) for e in evs)
+    total_ms_max = reduce_max(total_ms, ws, dev)
+    gates_step = circ.n_gates
+    gates_all = reduce_sum(gates_step * args.steps, ws, dev)
+    value = gates_all / (total_ms_max / 1e3)
+
+    # roofline of the gate-layer kernel (its launches dominate the step)
+    hbm, peak_kind = _peaks()
+    alg_bytes = np.mean([layer_bytes(circ.layer(l), n) for l in range(0, L, max(1, L // 50))])
+    per_launch_s = gate_ms / 1e3 / (args.steps * L)
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = None
+    if GATE_KERNEL_TRAFFIC["source_sha256"] == _kernel_hash():
+        traffic = GATE_KERNEL_TRAFFIC["bytes_per_launch"]
+
+    # end to end through the host-buffer C-ABI calls
+    e2e = run_e2e(args, qs, sim, circ, qubits, shots, seed, stream) if not args.no_e2e else None
+
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "gates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic",
+        "config": {
+            "workload": f"random Clifford circuit n={n} depth={L} p_cx=0.4 seed=3 "
+                        f"(final Z-measurement of all qubits)",
+            "step": f"init + {L} gate layers + first {M} of the {n} final measurements + "
+                    f"{shots}-shot frame sampling",
+            "gates_per_step": gates_step,
+            "measurements_per_step": M,
+            "shots_per_step": shots,
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "l2": "inputs larger than L2 (tableau 16.2 GB in each layout)",
+        },
+        "phases": {
+            "gate_layers": {"gates_per_s": gates_step * args.steps / (gate_ms / 1e3),
+                            "ms_per_step": gate_ms / args.steps},
+            "measurement": {"measurements_per_s": M * args.steps / (meas_ms / 1e3),
+                            "ms_per_step": meas_ms / args.steps,
+                            "includes": "column->row layout switch (2 transposes)"},
+            "sampling": {"shots_per_s": shots * args.steps / (samp_ms / 1e3),
+                         "ms_per_step": samp_ms / args.steps,
+                         "frame_gate_updates_per_s": gates_step * shots * args.steps /
+                         (samp_ms / 1e3)},
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "kernel": "gate_layer_kernel<true>",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": e2e,
+        "setup_s": {"generate_circuit": gen_s},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, circ)
+    if rank == 0:
+        print(json.dumps(out))
+    sim.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, qs, sim, circ, qubits, shots, seed, stream):
+    """Same step through the calls a user makes with host buffers: per-layer
+    qs_sim_apply_layer (host gate records -> pinned staging -> device),
+    qs_sim_measure with host qubits and host outcomes, qs_sim_sample into a
+    host record. Timed with CUDA events on the sim's stream around whole steps
+    (host->device and device->host copies inside)."""
+    import torch
+    n, L, M = circ.n, circ.n_layers, len(qubits)
+    layers = [np.ascontiguousarray(circ.layer(l)) for l in range(L)]
+    ow = (shots + 63) // 64
+    rec_host = np.zeros((M, ow), np.uint64)
+    fw_bytes = qs.qs_sim_sample_required_bytes(sim.sim, shots) + 2 * n * ((ow + 3) // 4 * 4) * 8
+    fws = torch.empty(fw_bytes, dtype=torch.uint8, device=sim.device)
+    steps = max(1, args.e2e_steps)
+
+    def step():
+        qs.qs_sim_reset(sim.sim, None)
+        for g in layers:
+            qs.qs_sim_apply_layer(sim.sim, g)
+        qs.qs_sim_measure(sim.sim, qubits, seed, 0, want_outcomes=True)
+        qs.qs_sim_sample(sim.sim, shots, seed + 7, rec_host.ctypes.data, M * ow, fws.data_ptr(),
+                         fw_bytes)
+
+    step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = a.elapsed_time(b)
+    h2d = circ.n_gates * 8 + M * 4
+    d2h = M + M * ow * 8
+    return {"value": circ.n_gates * steps / (ms / 1e3), "unit": "gates/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "steps": steps, "ms_per_step": ms / steps, "wall_s_per_step": wall / steps,
+            "path": "qs_sim_apply_layer (host gates) x L, qs_sim_measure (host outcomes), "
+                    "qs_sim_sample (host record)"}
+
+
+# ----------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ----------------------------------------------------------------------
+def oracle_gate_rate(circ, rows: int, layers: int, seed: int = 0):
+    """Oracle gates/s on the full n-qubit tableau, from a bounded sample: the
+    oracle's gate rules act on every one of the 2n rows independently
+    (Sec. 2.4), so `rows` sampled rows are evolved through `layers` layers and
+    the time is scaled by 2n / rows."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(seed)
+    n = circ.n
+    ids = np.sort(rng.choice(2 * n, size=rows, replace=False)).astype(np.uint32)
+    sub = O.RowSubset(n, ids)
+    g = circ.gates[:circ.layer_ptr[layers]]
+    t0 = time.perf_counter()
+    sub.apply(g)
+    dt = time.perf_counter() - t0
+    full_s = dt * (2 * n) / rows
+    return len(g) / full_s, dt, len(g)
+
+
+def oracle_measure_rate(n: int, layers: int, count: int):
+    """Oracle measurements/s on the same generator at a smaller n (the full
+    180k tableau does not fit the host memory of the oracle's unpacked rows)."""
+    from oracle import oracle as O
+    c = C.random_circuit(n, layers, 0.4, seed=3, final_measure_all=False)
+    o = O.Oracle(n)
+    o.apply(c.gates)
+    t0 = time.perf_counter()
+    o.measure(np.arange(count, dtype=np.uint32), seed=1)
+    dt = time.perf_counter() - t0
+    return count / dt, dt
+
+
+def cpu_baseline(args, circ):
+    rate, dt, g = oracle_gate_rate(circ, rows=args.cpu_rows, layers=args.cpu_layers)
+    mrate, mdt = oracle_measure_rate(args.cpu_meas_n, 40, args.cpu_meas_count)
+    return {"value": rate, "unit": "gates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{args.cpu_rows} of {2 * circ.n} generator rows through the first "
+                      f"{args.cpu_layers} layers ({g} gates) of the 180k circuit, scaled by "
+                      f"2n/rows ({dt:.1f} s of CPU)",
+            "measurements_per_s": mrate,
+            "measurements_sample": f"first {args.cpu_meas_count} final measurements after 40 "
+                                   f"layers of the same generator at n={args.cpu_meas_n} "
+                                   f"({mdt:.1f} s of CPU)",
+            "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    circ = C.random_circuit(args.n, max(args.cpu_layers, 1), 0.4, seed=3)
+    for _ in range(args.warmup):
+        oracle_gate_rate(circ, rows=16, layers=1)
+    t0 = time.perf_counter()
+    gates = 0
+    full_s = 0.0
+    for k in range(args.steps):
+        rate, dt, g = oracle_gate_rate(circ, rows=args.cpu_rows, layers=args.cpu_layers, seed=k)
+        gates += g
+        full_s += g / rate
+    wall = time.perf_counter() - t0
+    value = gates / full_s
+    out = {"metric": METRIC, "value": value, "unit": "gates/s", "impl": "reference",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": full_s * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+           "config": {"workload": f"random Clifford circuit n={args.n} depth=1000 p_cx=0.4 seed=3",
+                      "step": f"oracle gate rules on {args.cpu_rows} sampled generator rows "
+                              f"through {args.cpu_layers} layers, scaled to the full 2n rows"},
+           "cpu_baseline": {"value": value, "unit": "gates/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{args.cpu_rows} of {2 * args.n} rows x {args.cpu_layers} "
+                                      f"layers per step, {wall:.1f} s wall in total"},
+           "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_QUBITS)
+    ap.add_argument("--depth", type=int, default=DEPTH)
+    ap.add_argument("--measurements", type=int, default=64)
+    ap.add_argument("--shots", type=int, default=1024)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=64)
+    ap.add_argument("--cpu-layers", type=int, default=20)
+    ap.add_argument("--cpu-meas-n", type=int, default=2_000)
+    ap.add_argument("--cpu-meas-count", type=int, default=50)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
