@@ -218,6 +218,33 @@ int qs_sim_export_rows(qs_sim *sim, const uint32_t *rows, uint32_t count, uint64
  * ran out. */
 int qs_sim_sync(qs_sim *sim);
 
+/*
+ * Allocation-free variant of qs_sim_sample (the paper has no counterpart).
+ * For callers that cannot allocate device memory when they sample -- a
+ * serving process that reserved the GPU's memory for its own pool up front, a
+ * framework whose caching allocator must own every device byte, or a
+ * latency-critical loop that cannot afford cudaFree's device-wide
+ * synchronisation -- the frames are kept in one file-scope device array of
+ * QS_NOALLOC_SCRATCH_BYTES (32 MiB) inside libqs instead of a workspace.
+ * Output and sampling rule are those of qs_sim_sample; the call itself
+ * allocates nothing (no cudaMalloc/cudaFree, no allocating library routine).
+ *   record: host or device pointer of >= M * ceil(shots/64) words.
+ * Limits and behaviour:
+ *   - 2 * n * ceil(ceil(shots/64)/4)*4 * 8 bytes of frames (each rounded up to
+ *     256) plus M * ceil(shots/64) * 8 bytes must fit in the array, else
+ *     QS_ERR_SIZE with the sizes in qs_last_error().
+ *   - Every GPU that loads libqs holds the array until the process exits.
+ *   - All calls share the array and each call starts by clearing it (X~ = 0,
+ *     Z~ rewritten); two calls whose work overlaps on the GPU (different
+ *     streams, or different sims on one device) race on it. Calls from several
+ *     host threads are serialised on the host, not on the GPU.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ */
+#define QS_NOALLOC_SCRATCH_BYTES (32u << 20)
+int qs_sim_sample_noalloc(qs_sim *sim, uint64_t shots, uint64_t seed, uint64_t *record,
+                          size_t record_words);
+
 /* Number of kernel launches the sim has enqueued so far. */
 uint64_t qs_sim_launch_count(const qs_sim *sim);
 

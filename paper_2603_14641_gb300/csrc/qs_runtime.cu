@@ -665,3 +665,125 @@ int qs_sim_export_rows(qs_sim *s, const uint32_t *rows, uint32_t count, uint64_t
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free frame sampling (qs_sim_sample_noalloc in include/qs.h).
+//
+// Some callers cannot allocate device memory at the moment they want samples:
+// a serving process that reserved the whole GPU for its own pool up front, a
+// host framework whose caching allocator must own every byte, or a latency
+// loop that cannot take the device-wide synchronisation of cudaFree. For them
+// the Pauli frames live in one file-scope device array of fixed size instead
+// of a caller workspace or cudaMallocAsync. Every GPU that loads this library
+// holds the array until the process exits; all calls share it.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) uint64_t g_noalloc_frames[QS_NOALLOC_SCRATCH_BYTES / 8];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoallocMaxDevices] = {};
+// host bitmap used to cut measurement windows into runs of distinct qubits
+uint64_t g_noalloc_seen[(kMaxQubits + 63) / 64];
+}  // namespace
+
+extern "C" int qs_sim_sample_noalloc(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record,
+                                     size_t record_words) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (shots == 0) return fail(QS_ERR_ARG, "shots must be positive");
+  const uint32_t n = s->d.L.n;
+  const uint64_t M = s->n_meas;
+  const uint64_t ow = (shots + 63) / 64, fw = (ow + 3) / 4 * 4;
+  const size_t fbytes = (((size_t)n * fw * 8) + 255) & ~size_t(255);
+  const size_t need = 2 * fbytes + (size_t)std::max<uint64_t>(1, M) * ow * 8;
+  if (fw > 0xFFFFFFFFull || need > (size_t)QS_NOALLOC_SCRATCH_BYTES) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "qs_sim_sample_noalloc needs %zu bytes of frames for n = %u and %llu shots; the "
+             "static scratch holds %u bytes",
+             need, n, (unsigned long long)shots, (unsigned)QS_NOALLOC_SCRATCH_BYTES);
+    return fail(QS_ERR_SIZE, buf);
+  }
+  if (M && !record) return fail(QS_ERR_ARG, "record is NULL");
+  if (record_words < M * ow) return fail(QS_ERR_SIZE, "record smaller than M * ceil(shots/64) words");
+  int dev = 0;
+  QS_CUDA(s, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(QS_ERR_ARG, "device ordinal too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    // set-up, once per device with that device current: the host-side name of
+    // the array is not a device address, so ask the runtime for it
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_frames);
+    if (e != cudaSuccess || !p) return cuda_fail(s, e, "cudaGetSymbolAddress(g_noalloc_frames)");
+    g_noalloc_addr[dev] = p;
+  }
+  uint8_t *base = static_cast<uint8_t *>(g_noalloc_addr[dev]);
+  uint64_t *FX = reinterpret_cast<uint64_t *>(base);
+  uint64_t *FZ = reinterpret_cast<uint64_t *>(base + fbytes);
+  uint64_t *dout = reinterpret_cast<uint64_t *>(base + 2 * fbytes);
+  const bool out_dev = M ? is_device_ptr(record) : true;
+  uint64_t *out = out_dev ? record : dout;
+  // X~ is cleared to zero and Z~ fully rewritten by the init launch
+  QS_CUDA(s, launch_frame_init(FX, FZ, n, (uint32_t)fw, seed, s->stream));
+  s->launches += 1;
+  for (const Op &op : s->ops) {
+    if (op.kind == Op::kHostLayer) {
+      int slot;
+      uint8_t *h = ring_slot(s, &slot);
+      if (!h) return cuda_fail(s, cudaGetLastError(), "staging event");
+      memcpy(h, op.packed.data(), op.packed.size() * 4);
+      if ((rc = upload(s, slot, op.packed.size() * 4))) return rc;
+      QS_CUDA(s, launch_frame_layer(FX, FZ, n, (uint32_t)fw, reinterpret_cast<uint32_t *>(s->dstage),
+                                    (uint32_t)(op.packed.size() / 2), s->d.err, s->stream));
+      s->launches += 1;
+    } else if (op.kind == Op::kDevLayers) {
+      for (size_t l = 0; l + 1 < op.ptr.size(); ++l) {
+        const int64_t a = op.ptr[l], cnt = op.ptr[l + 1] - a;
+        QS_CUDA(s, launch_frame_layer(FX, FZ, n, (uint32_t)fw, op.dev + 2 * a, (uint32_t)cnt,
+                                      s->d.err, s->stream));
+        if (cnt) s->launches += 1;
+      }
+    } else if (op.kind == Op::kDevMeasure) {
+      // the list stays on the device: one launch per measurement keeps repeated
+      // qubits in program order without reading the list back
+      for (uint32_t i = 0; i < op.count; ++i) {
+        QS_CUDA(s, launch_frame_measure(FX, FZ, n, (uint32_t)fw, op.dev + i, 1, op.m0 + i,
+                                        s->d.record, out, shots, seed, s->d.err, s->stream));
+        s->launches += 1;
+      }
+    } else {
+      const uint32_t *qh = op.qubits.data();
+      const uint32_t cnt = (uint32_t)op.qubits.size();
+      const uint32_t chunk = (uint32_t)(s->plan.stage_bytes / 4);
+      uint32_t start = 0;
+      while (start < cnt) {
+        uint32_t end = start;
+        while (end < cnt && end - start < chunk &&
+               !((g_noalloc_seen[qh[end] >> 6] >> (qh[end] & 63)) & 1u)) {
+          g_noalloc_seen[qh[end] >> 6] |= 1ull << (qh[end] & 63);
+          ++end;
+        }
+        for (uint32_t i = start; i < end; ++i) g_noalloc_seen[qh[i] >> 6] = 0;
+        int slot;
+        uint8_t *h = ring_slot(s, &slot);
+        if (!h) return cuda_fail(s, cudaGetLastError(), "staging event");
+        memcpy(h, qh + start, (size_t)(end - start) * 4);
+        if ((rc = upload(s, slot, (size_t)(end - start) * 4))) return rc;
+        QS_CUDA(s, launch_frame_measure(FX, FZ, n, (uint32_t)fw,
+                                        reinterpret_cast<uint32_t *>(s->dstage), end - start,
+                                        op.m0 + start, s->d.record, out, shots, seed, s->d.err,
+                                        s->stream));
+        s->launches += (end - start + 65534) / 65535;
+        start = end;
+      }
+    }
+  }
+  if (!out_dev && M)
+    QS_CUDA(s, cudaMemcpyAsync(record, dout, (size_t)(M * ow * 8), cudaMemcpyDeviceToHost, s->stream));
+  if (!out_dev) return qs_sim_sync(s);
+  return QS_OK;
+}

@@ -67,6 +67,7 @@ SIGNATURES = {
     "qs_sim_sample_required_bytes": (_sz, [_vp, _u64]),
     "qs_sim_sample": (ctypes.c_int, [_vp, _u64, _u64, _vp, _sz, _vp, _sz]),
     "qs_sim_tableau_export": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _sz, ctypes.POINTER(_sz)]),
+    "qs_sim_sample_noalloc": (ctypes.c_int, [_vp, _u64, _u64, _vp, _sz]),
     "qs_sim_export_rows": (ctypes.c_int, [_vp, _vp, _u32, _vp]),
     "qs_sim_sync": (ctypes.c_int, [_vp]),
     "qs_sim_launch_count": (_u64, [_vp]),
@@ -196,6 +197,14 @@ def qs_sim_sample(sim: int, shots: int, seed: int, record: int, record_words: in
     _check(lib().qs_sim_sample(ctypes.c_void_p(sim), shots, seed, ctypes.c_void_p(record or None),
                                record_words, ctypes.c_void_p(frame_ws or None), frame_ws_bytes),
            "qs_sim_sample")
+
+
+def qs_sim_sample_noalloc(sim: int, shots: int, seed: int, record: int, record_words: int) -> None:
+    """qs_sim_sample with the frames in libqs's fixed static device array
+    (allocates nothing; see include/qs.h for the size limit and sharing)."""
+    _check(lib().qs_sim_sample_noalloc(ctypes.c_void_p(sim), shots, seed,
+                                       ctypes.c_void_p(record or None), record_words),
+           "qs_sim_sample_noalloc")
 
 
 def qs_sim_tableau_export(sim: int) -> np.ndarray:
