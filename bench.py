@@ -47,7 +47,8 @@ FALLBACK_HBM_GBS = 6800.0
 
 # ncu DRAM traffic of one gate-layer launch on the 180k workload, and the hash
 # of the kernel source it was taken with (null once the kernel changes).
-GATE_KERNEL_TRAFFIC = {"bytes_per_launch": None, "source_sha256": None}
+GATE_KERNEL_TRAFFIC = {"bytes_per_launch": 13306932992 + 8059148288,
+                       "source_sha256": "d925673a3569f3484b166edd0bc60a6103c6713db8c6db341f8ae7e6b39921ed"}
 
 
 def _kernel_hash() -> str:
@@ -173,6 +174,23 @@ def layer_bytes(gates: np.ndarray, n: int) -> float:
 # ----------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------
+WORKLOADS = {
+    "n180k": lambda a: C.random_circuit(a.n, a.depth, 0.4, seed=3, name="n180k_d1000"),
+    "n10k": lambda a: C.workload_10k(),
+    "n256": lambda a: C.workload_256(),
+}
+
+
+def step_program(circ, max_final: int):
+    """The circuit's ops, with the last measurement window cut to its first
+    `max_final` qubits when max_final > 0 (the full final measurement of a
+    180k-qubit circuit does not fit a bounded step)."""
+    ops = list(circ.ops)
+    if max_final > 0 and ops and ops[-1][0] == "measure":
+        ops[-1] = ("measure", np.asarray(ops[-1][1][:max_final], np.uint32))
+    return ops
+
+
 def run_ours(args):
     import torch
     from paper_2603_14641_gb300 import qs
@@ -185,46 +203,53 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     t_gen = time.time()
-    circ = C.random_circuit(args.n, args.depth, 0.4, seed=3, name="n180k_d1000")
+    circ = WORKLOADS[args.workload](args)
     gen_s = time.time() - t_gen
     n, L = circ.n, circ.n_layers
-    M, shots = args.measurements, args.shots
+    shots = args.shots
     seed = 1234 + rank
+    prog = step_program(circ, args.measurements if args.workload == "n180k" else 0)
+    M = int(sum(len(op[1]) for op in prog if op[0] == "measure"))
 
     stream = torch.cuda.Stream(device=dev)
-    sim = qs.Simulator(n, device=str(dev), stream=stream)
+    flags = qs.QS_FLAG_NO_FUSION if args.no_fusion else 0
+    sim = qs.Simulator(n, device=str(dev), stream=stream, flags=flags)
     packed_host = qs.qs_pack_layers(n, circ.gates, circ.layer_ptr)
     packed_dev = torch.from_numpy(packed_host.view(np.int32)).to(dev)
     lp = np.asarray(circ.layer_ptr, np.int64)
-    qubits = np.arange(M, dtype=np.uint32)  # the final measurement goes in ascending order
-    q_dev = torch.from_numpy(qubits.view(np.int32)).to(dev)
+    qdev = [torch.from_numpy(np.asarray(op[1], np.uint32).view(np.int32)).to(dev)
+            if op[0] == "measure" else None for op in prog]
     ow = (shots + 63) // 64
-    rec_dev = torch.zeros((M, ow), dtype=torch.int64, device=dev)
-    # frame workspace for the step's op log (sim op log holds L layers + M measurements)
+    rec_dev = torch.zeros((max(M, 1), ow), dtype=torch.int64, device=dev)
     fw_bytes = 2 * n * ((ow + 3) // 4 * 4) * 8 + max(M, 1) * ow * 8 + 4096
     fws = torch.empty(fw_bytes, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
 
     def step(ev):
+        """ev: list of (kind, start event, end event) filled in program order."""
         qs.qs_sim_reset(sim.sim, None)
-        ev[0].record(stream)
-        qs.qs_sim_apply_layers_dev(sim.sim, packed_dev.data_ptr(), lp, 0, L)
-        ev[1].record(stream)
-        qs.qs_sim_measure_dev(sim.sim, q_dev.data_ptr(), M, seed, 0)
-        ev[2].record(stream)
+        for op, qd in zip(prog, qdev):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if op[0] == "layers":
+                qs.qs_sim_apply_layers_dev(sim.sim, packed_dev.data_ptr(), lp, op[1], op[2])
+            else:
+                qs.qs_sim_measure_dev(sim.sim, qd.data_ptr(), qd.numel(), seed, 0)
+            b.record(stream)
+            ev.append((op[0], a, b))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         qs.qs_sim_sample(sim.sim, shots, seed + 7, rec_dev.data_ptr(), M * ow, fws.data_ptr(),
                          fw_bytes)
-        ev[3].record(stream)
-
-    def mk():
-        return [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        b.record(stream)
+        ev.append(("sample", a, b))
 
     for _ in range(args.warmup):
-        step(mk())
+        step([])
     qs.qs_sim_sync(sim.sim)
     torch.cuda.synchronize()
 
-    evs = [mk() for _ in range(args.steps)]
+    evs = [[] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = qs.qs_sim_launch_count(sim.sim)
     with ClockSampler(local) as clk:
@@ -239,9 +264,11 @@ def run_ours(args):
     launches = qs.qs_sim_launch_count(sim.sim) - launches0
     qs.qs_sim_sync(sim.sim)  # device self-checks
     total_ms = start.elapsed_time(end)
-    gate_ms = sum(e[0].elapsed_time(e[1]) for e in evs)
-    meas_ms = sum(e[1].elapsed_time(e[2]) for e in evs)
-    samp_ms = sum(e[2].elapsed_time(e[3]) for e in evs)
+    ph = {"layers": 0.0, "measure": 0.0, "sample": 0.0}
+    for ev in evs:
+        for kind, a, b in ev:
+            ph[kind] += a.elapsed_time(b)
+    gate_ms, meas_ms, samp_ms = ph["layers"], ph["measure"], ph["sample"]
     total_ms_max = reduce_max(total_ms, ws, dev)
     gates_step = circ.n_gates
     gates_all = reduce_sum(gates_step * args.steps, ws, dev)
@@ -249,15 +276,18 @@ def run_ours(args):
 
     # roofline of the gate-layer kernel (its launches dominate the step)
     hbm, peak_kind = _peaks()
-    alg_bytes = np.mean([layer_bytes(circ.layer(l), n) for l in range(0, L, max(1, L // 50))])
+    alg_bytes = float(np.mean([layer_bytes(circ.layer(l), n) for l in range(0, L, max(1, L // 50))]))
     per_launch_s = gate_ms / 1e3 / (args.steps * L)
     achieved = alg_bytes / per_launch_s / 1e9
+    fused = n * 16 <= 220 * 1024 and not args.no_fusion
     traffic = None
-    if GATE_KERNEL_TRAFFIC["source_sha256"] == _kernel_hash():
+    if not fused and GATE_KERNEL_TRAFFIC["source_sha256"] == _kernel_hash() and \
+            args.workload == "n180k":
         traffic = GATE_KERNEL_TRAFFIC["bytes_per_launch"]
 
-    # end to end through the host-buffer C-ABI calls
-    e2e = run_e2e(args, qs, sim, circ, qubits, shots, seed, stream) if not args.no_e2e else None
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, qs, sim, circ, prog, shots, seed, stream)
 
     clocks = clk.summary()
     out = {
@@ -274,22 +304,26 @@ def run_ours(args):
         "dtype": "u64",
         "data": "synthetic",
         "config": {
-            "workload": f"random Clifford circuit n={n} depth={L} p_cx=0.4 seed=3 "
-                        f"(final Z-measurement of all qubits)",
-            "step": f"init + {L} gate layers + first {M} of the {n} final measurements + "
-                    f"{shots}-shot frame sampling",
+            "workload": f"random Clifford circuit {circ.name}: n={n} depth={L} "
+                        f"({circ.n_measurements} Z-measurements in the full program)",
+            "step": f"init + {L} gate layers + {M} measurements"
+                    + (f" (the first {M} of the {n} final measurements)"
+                       if args.workload == "n180k" else "")
+                    + f" + {shots}-shot frame sampling",
             "gates_per_step": gates_step,
             "measurements_per_step": M,
             "shots_per_step": shots,
+            "fused_segments": fused,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-            "l2": "inputs larger than L2 (tableau 16.2 GB in each layout)",
+            "l2": ("inputs larger than L2 (tableau 16.2 GB in each layout)" if n >= 20_000
+                   else "tableau smaller than L2 (no flush: L2-resident by design)"),
         },
         "phases": {
             "gate_layers": {"gates_per_s": gates_step * args.steps / (gate_ms / 1e3),
                             "ms_per_step": gate_ms / args.steps},
-            "measurement": {"measurements_per_s": M * args.steps / (meas_ms / 1e3),
+            "measurement": {"measurements_per_s": M * args.steps / (meas_ms / 1e3) if M else None,
                             "ms_per_step": meas_ms / args.steps,
-                            "includes": "column->row layout switch (2 transposes)"},
+                            "includes": "column->row layout switch (2 transposes) per window"},
             "sampling": {"shots_per_s": shots * args.steps / (samp_ms / 1e3),
                          "ms_per_step": samp_ms / args.steps,
                          "frame_gate_updates_per_s": gates_step * shots * args.steps /
@@ -297,8 +331,10 @@ def run_ours(args):
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": "gate_layer_kernel<true>",
+                     "kernel": "fused_segment_kernel<true>" if fused else "gate_layer_kernel<true>",
                      "algorithmic_bytes_per_launch": alg_bytes,
+                     "note": ("fused: algorithmic bytes are the unfused per-layer bytes, so frac "
+                              "is an effective rate" if fused else "per-layer kernel"),
                      "peak_source": f"{peak_kind} hbm_gbs"},
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -315,26 +351,30 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, qs, sim, circ, qubits, shots, seed, stream):
+def run_e2e(args, qs, sim, circ, prog, shots, seed, stream):
     """Same step through the calls a user makes with host buffers: per-layer
     qs_sim_apply_layer (host gate records -> pinned staging -> device),
     qs_sim_measure with host qubits and host outcomes, qs_sim_sample into a
     host record. Timed with CUDA events on the sim's stream around whole steps
     (host->device and device->host copies inside)."""
     import torch
-    n, L, M = circ.n, circ.n_layers, len(qubits)
-    layers = [np.ascontiguousarray(circ.layer(l)) for l in range(L)]
+    n = circ.n
+    M = int(sum(len(op[1]) for op in prog if op[0] == "measure"))
+    layers = [np.ascontiguousarray(circ.layer(l)) for l in range(circ.n_layers)]
     ow = (shots + 63) // 64
-    rec_host = np.zeros((M, ow), np.uint64)
-    fw_bytes = qs.qs_sim_sample_required_bytes(sim.sim, shots) + 2 * n * ((ow + 3) // 4 * 4) * 8
+    rec_host = np.zeros((max(M, 1), ow), np.uint64)
+    fw_bytes = 2 * n * ((ow + 3) // 4 * 4) * 8 + max(M, 1) * ow * 8 + 4096
     fws = torch.empty(fw_bytes, dtype=torch.uint8, device=sim.device)
     steps = max(1, args.e2e_steps)
 
     def step():
         qs.qs_sim_reset(sim.sim, None)
-        for g in layers:
-            qs.qs_sim_apply_layer(sim.sim, g)
-        qs.qs_sim_measure(sim.sim, qubits, seed, 0, want_outcomes=True)
+        for op in prog:
+            if op[0] == "layers":
+                for l in range(op[1], op[2]):
+                    qs.qs_sim_apply_layer(sim.sim, layers[l])
+            else:
+                qs.qs_sim_measure(sim.sim, op[1], seed, 0, want_outcomes=True)
         qs.qs_sim_sample(sim.sim, shots, seed + 7, rec_host.ctypes.data, M * ow, fws.data_ptr(),
                          fw_bytes)
 
@@ -355,7 +395,7 @@ def run_e2e(args, qs, sim, circ, qubits, shots, seed, stream):
     return {"value": circ.n_gates * steps / (ms / 1e3), "unit": "gates/s",
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "steps": steps, "ms_per_step": ms / steps, "wall_s_per_step": wall / steps,
-            "path": "qs_sim_apply_layer (host gates) x L, qs_sim_measure (host outcomes), "
+            "path": "qs_sim_apply_layer (host gates) per layer, qs_sim_measure (host outcomes), "
                     "qs_sim_sample (host record)"}
 
 
@@ -407,6 +447,86 @@ def cpu_baseline(args, circ):
             "host_cores_available": os.cpu_count()}
 
 
+def run_batch(args):
+    """Batched workload: 512 independent circuits (n log-uniform 50..5,000,
+    depth 200, 10% of qubits measured after every 10th layer) in one
+    persistent launch, against the same circuits run one at a time through the
+    single-circuit path on the same GPU (a seeded subset of every 8th circuit
+    for the one-at-a-time leg, whose launches take tens of seconds for all 512)."""
+    import torch
+    from paper_2603_14641_gb300 import qs
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    circs = C.batch_workload(args.batch_count)
+    seeds = [5000 + i for i in range(len(circs))]
+    gates = sum(c.n_gates for c in circs)
+    meas = sum(c.n_measurements for c in circs)
+    stream = torch.cuda.Stream(device=dev)
+    b = qs.Batch(circs, seeds, device=str(dev), stream=stream)
+    tune_path = os.path.join("/tmp", "qs_batch_tuning.txt")
+    t0 = time.time()
+    tuning = b.autotune(round_limit=2, cache_path=tune_path)
+    tune_s = time.time() - t0
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / steps
+
+    ms_batch = timed(lambda: b.run(tuning), args.steps, args.warmup)
+    b.sync()
+    # one circuit at a time through the single-circuit path (subset)
+    idx = list(range(0, len(circs), 8))
+    sub = [circs[i] for i in idx]
+    bs = qs.Batch(sub, [seeds[i] for i in idx], device=str(dev), stream=stream)
+    ms_batch_sub = timed(lambda: bs.run(tuning), args.steps, args.warmup)
+    bs.sync()
+    sims, dcs, qd = [], [], []
+    for c in sub:
+        s_ = qs.Simulator(c.n, device=str(dev), stream=stream)
+        sims.append(s_)
+        dcs.append(s_.upload(c))
+        qd.append([torch.from_numpy(np.asarray(op[1], np.uint32).view(np.int32)).to(dev)
+                   if op[0] == "measure" else None for op in c.ops])
+
+    def one_at_a_time():
+        for s_, c, dc, qq, i in zip(sims, sub, dcs, qd, idx):
+            qs.qs_sim_reset(s_.sim, None)
+            for op, q in zip(c.ops, qq):
+                if op[0] == "layers":
+                    qs.qs_sim_apply_layers_dev(s_.sim, dc.packed.data_ptr(), dc.layer_ptr, op[1], op[2])
+                else:
+                    qs.qs_sim_measure_dev(s_.sim, q.data_ptr(), q.numel(), seeds[i], 0)
+
+    ms_single_sub = timed(one_at_a_time, 1, 1)
+    identical = all(np.array_equal(s_.record(), b.record(i)) for s_, i in zip(sims, idx))
+    g_sub = sum(c.n_gates for c in sub)
+    m_sub = sum(c.n_measurements for c in sub)
+    out = {"metric": "batched Clifford circuits: gates/s and measurements/s, one persistent "
+                     "launch vs one circuit at a time",
+           "value": gates / (ms_batch / 1e3), "unit": "gates/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic",
+           "config": {"workload": f"{len(circs)} random Clifford circuits, n log-uniform "
+                                  "50..5000, depth 200, p_cx 0.5, 10% measured every 10 layers",
+                      "gates": gates, "measurements": meas,
+                      "tuning": tuning.as_dict(), "autotune_s": tune_s},
+           "measurements_per_s": meas / (ms_batch / 1e3),
+           "subset": {"circuits": len(sub), "gates": g_sub, "measurements": m_sub,
+                      "batch_ms": ms_batch_sub, "one_at_a_time_ms": ms_single_sub,
+                      "speedup": ms_single_sub / ms_batch_sub,
+                      "records_identical": bool(identical)}}
+    print(json.dumps(out))
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -444,6 +564,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n180k", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--no-fusion", action="store_true")
     ap.add_argument("--n", type=int, default=N_QUBITS)
     ap.add_argument("--depth", type=int, default=DEPTH)
     ap.add_argument("--measurements", type=int, default=64)
@@ -460,6 +583,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

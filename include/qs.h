@@ -70,9 +70,14 @@ typedef struct qs_key {
 
 typedef struct qs_options {
   uint64_t record_capacity; /* max measurements kept in the device record; 0 = 16 n + 65536 */
-  uint32_t flags;           /* reserved, 0 */
+  uint32_t flags;           /* QS_FLAG_* bits, 0 for defaults */
   uint32_t reserved;
 } qs_options;
+
+/* qs_options.flags: apply every device-resident layer with its own kernel
+ * instead of fusing a run of layers into one shared-memory pass (the fused
+ * pass is used for n <= 14,080; results are identical either way). */
+#define QS_FLAG_NO_FUSION 1u
 
 typedef struct qs_sim qs_sim;
 
@@ -244,6 +249,88 @@ int qs_sim_sync(qs_sim *sim);
 #define QS_NOALLOC_SCRATCH_BYTES (32u << 20)
 int qs_sim_sample_noalloc(qs_sim *sim, uint64_t shots, uint64_t seed, uint64_t *record,
                           size_t record_words);
+
+/* ---------------------------------------------------------------------- */
+/* Batched persistent launch: many independent circuits, one kernel launch */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * One circuit of a batch, as a program of rounds: round r applies layers
+ * [round_layers[r], round_layers[r+1]) (each layer a window of gates on
+ * disjoint qubits, Sec. 4.2) and then measures, in order,
+ * qubits[round_meas[r] .. round_meas[r+1]) in the Z basis (CHP, Sec. 2.5).
+ * The coin of the circuit's m-th measurement (program order) is keyed by
+ * (seed, shot, m) exactly as in qs_sim_measure, so a circuit's record and
+ * tableau are the same alone (qs_sim_*) and in a batch. All arrays are host
+ * memory and are copied at qs_batch_create. n <= 8192.
+ */
+typedef struct qs_batch_circuit {
+  uint32_t n;
+  uint32_t n_layers;
+  const qs_gate *gates;          /* layer l = gates[layer_ptr[l] .. layer_ptr[l+1]) */
+  const int64_t *layer_ptr;      /* n_layers + 1 offsets */
+  uint32_t n_rounds;
+  uint32_t reserved;
+  const uint32_t *round_layers;  /* n_rounds + 1 layer offsets, [0] = 0 */
+  const uint32_t *round_meas;    /* n_rounds + 1 offsets into qubits, [0] = 0 */
+  const uint32_t *qubits;        /* round_meas[n_rounds] measured qubits */
+  uint64_t seed, shot;           /* key of the circuit's coins */
+} qs_batch_circuit;
+
+/* Launch shape of the persistent kernel (qs_batch_autotune picks one).
+ *   threads:         256, 512 or 1024 per CTA
+ *   blocks_per_sm:   CTAs per SM (0 = as many as fit)
+ *   words_per_block: 64-row column words per shared-memory slice in the gate phase (1 or 2)
+ *   fuse_depth:      layers per shared-memory pass in the gate phase (0 = whole round)
+ *   spin_limit:      bound on each grid-barrier spin (0 = default, several seconds); when it
+ *                    runs out the kernel stops and qs_batch_sync returns QS_ERR_TIMEOUT */
+typedef struct qs_batch_tuning {
+  uint32_t threads;
+  uint32_t blocks_per_sm;
+  uint32_t words_per_block;
+  uint32_t fuse_depth;
+  uint64_t spin_limit;
+} qs_batch_tuning;
+
+typedef struct qs_batch qs_batch;
+
+/* Device bytes of a batch (0 if the description is invalid). */
+size_t qs_batch_required_bytes(uint32_t count, const qs_batch_circuit *circuits);
+
+/* Validates (as qs_pack_layers; measured qubits < n; offsets in range) and
+ * uploads the batch. workspace: caller device memory of >= required bytes,
+ * 256-byte aligned, or NULL to let the library cudaMalloc it. */
+int qs_batch_create(uint32_t count, const qs_batch_circuit *circuits, void *cuda_stream,
+                    void *workspace, size_t workspace_bytes, qs_batch **out);
+
+int qs_batch_destroy(qs_batch *batch);
+
+/* Runs every circuit from |0...0> through its rounds (the first round_limit
+ * rounds, 0 = all) in one cooperative persistent kernel launch on the
+ * batch's stream. tuning: NULL for the default shape. Asynchronous. */
+int qs_batch_run(qs_batch *batch, const qs_batch_tuning *tuning, uint32_t round_limit);
+
+/* Waits for the batch's stream; QS_ERR_TIMEOUT if a grid barrier ran out,
+ * QS_ERR_INTERNAL if a device self-check failed. */
+int qs_batch_sync(qs_batch *batch);
+
+/* Copies the first `count` record entries (0/1 bytes) of one circuit. Syncs. */
+int qs_batch_record(qs_batch *batch, uint32_t circuit, uint8_t *dst, size_t count);
+
+/* Selected generator rows of one circuit, in the format of qs_sim_export_rows. Syncs. */
+int qs_batch_export_rows(qs_batch *batch, uint32_t circuit, const uint32_t *rows, uint32_t count,
+                         uint64_t *dst);
+
+/* Times the candidate launch shapes on this batch (the first round_limit
+ * rounds; 0 = all) and returns the fastest. cache_path: NULL, or a text file
+ * of "device|batch-signature|rounds threads blocks_per_sm words_per_block
+ * fuse_depth" lines that is read first and appended to. Results do not depend
+ * on the shape. */
+int qs_batch_autotune(qs_batch *batch, uint32_t round_limit, const char *cache_path,
+                      qs_batch_tuning *best);
+
+/* Message for the last batch error on the calling thread. */
+const char *qs_batch_last_error(void);
 
 /* Number of kernel launches the sim has enqueued so far. */
 uint64_t qs_sim_launch_count(const qs_sim *sim);

@@ -119,5 +119,11 @@ cudaError_t launch_frame_measure(uint64_t *FX, uint64_t *FZ, uint32_t n, uint32_
                                  const uint8_t *ref, uint64_t *out, uint64_t shots, uint64_t seed,
                                  uint32_t *err, cudaStream_t s);
 cudaError_t launch_reset_meas_state(const Dev &d, cudaStream_t s);
+// fused segment of L layers on a word-sliced, shared-memory-resident tableau
+// (S == nullptr: frames, no signs); lptr: L + 1 device gate offsets
+bool fused_fits(uint32_t n);
+cudaError_t launch_fused_segment(uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t n, uint32_t stride,
+                                 uint32_t nwords, const uint32_t *packed, const int64_t *lptr,
+                                 uint32_t L, uint32_t *err, cudaStream_t s);
 
 }  // namespace qs

@@ -104,6 +104,7 @@ struct qs_sim {
   std::vector<uint32_t> stamp;
   uint32_t stamp_id = 0;
   uint64_t launches = 0;
+  uint32_t flags = 0;
 };
 
 namespace {
@@ -194,6 +195,44 @@ int validate_pack(uint32_t n, const qs_gate *g, size_t count, std::vector<uint32
   return QS_OK;
 }
 
+// Enqueues layers [0, ptr.size() - 1) given by absolute gate offsets `ptr`
+// of device gate records `packed` on the tableau (S != nullptr) or on frames.
+// Runs of layers go through the fused shared-memory kernel when the word slice
+// fits, else one kernel per layer.
+int run_dev_layers(qs_sim *s, uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t stride,
+                   const uint32_t *packed, const int64_t *ptr, size_t nlayers, bool tableau) {
+  const uint32_t n = s->d.L.n;
+  if (nlayers == 0) return QS_OK;
+  if (fused_fits(n) && !(s->flags & QS_FLAG_NO_FUSION)) {
+    const size_t cap = s->plan.stage_bytes / 8 - 1;  // layers per staged offset table
+    for (size_t l0 = 0; l0 < nlayers; l0 += cap) {
+      const size_t L = std::min(cap, nlayers - l0);
+      int slot;
+      uint8_t *h = ring_slot(s, &slot);
+      if (!h) return cuda_fail(s, cudaGetLastError(), "staging event");
+      memcpy(h, ptr + l0, (L + 1) * 8);
+      int rc = upload(s, slot, (L + 1) * 8);
+      if (rc) return rc;
+      QS_CUDA(s, launch_fused_segment(X, Z, S, n, stride, stride, packed,
+                                      reinterpret_cast<const int64_t *>(s->dstage), (uint32_t)L,
+                                      s->d.err, s->stream));
+      s->launches += 1;
+    }
+    return QS_OK;
+  }
+  for (size_t l = 0; l < nlayers; ++l) {
+    const int64_t a = ptr[l], cnt = ptr[l + 1] - a;
+    if (cnt == 0) continue;
+    if (tableau)
+      QS_CUDA(s, launch_gate_layer(s->d, packed + 2 * a, (uint32_t)cnt, s->stream));
+    else
+      QS_CUDA(s, launch_frame_layer(X, Z, n, stride, packed + 2 * a, (uint32_t)cnt, s->d.err,
+                                    s->stream));
+    s->launches += 1;
+  }
+  return QS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -219,6 +258,7 @@ int qs_sim_create(uint32_t n, const qs_options *opt, void *cuda_stream, void *wo
   s->d.L = make_layout(n);
   s->plan = make_plan(s->d.L, opt);
   s->stream = static_cast<cudaStream_t>(cuda_stream);
+  s->flags = opt ? opt->flags : 0u;
   if (workspace) {
     if (workspace_bytes < s->plan.total) {
       delete s;
@@ -368,12 +408,13 @@ int qs_sim_apply_layers_dev(qs_sim *s, const uint32_t *packed_dev, const int64_t
   op.kind = Op::kDevLayers;
   op.dev = packed_dev;
   op.ptr.assign(layer_ptr + l_begin, layer_ptr + l_end + 1);
-  for (uint32_t l = l_begin; l < l_end; ++l) {
-    const int64_t a = layer_ptr[l], cnt = layer_ptr[l + 1] - a;
+  for (size_t l = 0; l + 1 < op.ptr.size(); ++l) {
+    const int64_t cnt = op.ptr[l + 1] - op.ptr[l];
     if (cnt < 0 || cnt > (int64_t)s->d.L.n) return fail(QS_ERR_ARG, "bad layer_ptr");
-    QS_CUDA(s, launch_gate_layer(s->d, packed_dev + 2 * a, (uint32_t)cnt, s->stream));
-    if (cnt) s->launches += 1;
   }
+  if ((rc = run_dev_layers(s, s->d.X, s->d.Z, s->d.S, s->d.L.cs, packed_dev, op.ptr.data(),
+                           op.ptr.size() - 1, true)))
+    return rc;
   s->rows_valid = false;
   s->ops.push_back(std::move(op));
   return QS_OK;
@@ -551,12 +592,9 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
                                     (uint32_t)(op.packed.size() / 2), s->d.err, s->stream));
       s->launches += 1;
     } else if (op.kind == Op::kDevLayers) {
-      for (size_t l = 0; l + 1 < op.ptr.size(); ++l) {
-        const int64_t a = op.ptr[l], cnt = op.ptr[l + 1] - a;
-        QS_CUDA(s, launch_frame_layer(FX, FZ, n, (uint32_t)fw, op.dev + 2 * a, (uint32_t)cnt,
-                                      s->d.err, s->stream));
-        if (cnt) s->launches += 1;
-      }
+      if ((rc = run_dev_layers(s, FX, FZ, nullptr, (uint32_t)fw, op.dev, op.ptr.data(),
+                               op.ptr.size() - 1, false)))
+        return rc;
     } else {
       // measurement window: split into runs of distinct qubits (Sec. 5 processes
       // the measurements of one window in parallel)

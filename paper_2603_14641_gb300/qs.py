@@ -44,6 +44,23 @@ class qs_gate(ctypes.Structure):
     _fields_ = [("type", ctypes.c_uint32), ("q0", ctypes.c_uint32), ("q1", ctypes.c_uint32)]
 
 
+class qs_batch_circuit(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("n_layers", ctypes.c_uint32),
+                ("gates", ctypes.c_void_p), ("layer_ptr", ctypes.c_void_p),
+                ("n_rounds", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("round_layers", ctypes.c_void_p), ("round_meas", ctypes.c_void_p),
+                ("qubits", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("shot", ctypes.c_uint64)]
+
+
+class qs_batch_tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("words_per_block", ctypes.c_uint32), ("fuse_depth", ctypes.c_uint32),
+                ("spin_limit", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _vp = ctypes.c_void_p
 _u64 = ctypes.c_uint64
 _u32 = ctypes.c_uint32
@@ -71,6 +88,15 @@ SIGNATURES = {
     "qs_sim_export_rows": (ctypes.c_int, [_vp, _vp, _u32, _vp]),
     "qs_sim_sync": (ctypes.c_int, [_vp]),
     "qs_sim_launch_count": (_u64, [_vp]),
+    "qs_batch_required_bytes": (_sz, [_u32, _vp]),
+    "qs_batch_create": (ctypes.c_int, [_u32, _vp, _vp, _vp, _sz, ctypes.POINTER(_vp)]),
+    "qs_batch_destroy": (ctypes.c_int, [_vp]),
+    "qs_batch_run": (ctypes.c_int, [_vp, _vp, _u32]),
+    "qs_batch_sync": (ctypes.c_int, [_vp]),
+    "qs_batch_record": (ctypes.c_int, [_vp, _u32, _vp, _sz]),
+    "qs_batch_export_rows": (ctypes.c_int, [_vp, _u32, _vp, _u32, _vp]),
+    "qs_batch_autotune": (ctypes.c_int, [_vp, _u32, ctypes.c_char_p, _vp]),
+    "qs_batch_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -111,14 +137,17 @@ def qs_version() -> str:
     return lib().qs_version().decode()
 
 
+QS_FLAG_NO_FUSION = 1
+
+
 def qs_sim_required_bytes(n: int, record_capacity: int = 0) -> int:
     opt = qs_options(record_capacity, 0, 0)
     return int(lib().qs_sim_required_bytes(n, ctypes.byref(opt)))
 
 
 def qs_sim_create(n: int, stream: int = 0, workspace: int = 0, workspace_bytes: int = 0,
-                  record_capacity: int = 0) -> int:
-    opt = qs_options(record_capacity, 0, 0)
+                  record_capacity: int = 0, flags: int = 0) -> int:
+    opt = qs_options(record_capacity, flags, 0)
     h = ctypes.c_void_p()
     _check(lib().qs_sim_create(n, ctypes.byref(opt), ctypes.c_void_p(stream or None),
                                ctypes.c_void_p(workspace or None), workspace_bytes,
@@ -267,7 +296,8 @@ class DeviceCircuit:
 
 
 class Simulator:
-    def __init__(self, n: int, device: str = "cuda", stream=None, record_capacity: int = 0):
+    def __init__(self, n: int, device: str = "cuda", stream=None, record_capacity: int = 0,
+                 flags: int = 0):
         import torch
         self.torch = torch
         self.n = int(n)
@@ -276,7 +306,7 @@ class Simulator:
         nbytes = qs_sim_required_bytes(self.n, record_capacity)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.sim = qs_sim_create(self.n, self.stream.cuda_stream, self.workspace.data_ptr(), nbytes,
-                                 record_capacity)
+                                 record_capacity, flags)
         self._keep = []
 
     def close(self):
@@ -360,3 +390,117 @@ class Simulator:
     @property
     def launch_count(self) -> int:
         return qs_sim_launch_count(self.sim)
+
+
+# ----------------------------------------------------------------------
+# Batched persistent launch
+# ----------------------------------------------------------------------
+
+def _bcheck(rc: int, where: str) -> None:
+    if rc != QS_OK:
+        raise QsError(rc, where, lib().qs_batch_last_error().decode())
+
+
+def circuit_rounds(circuit):
+    """Rounds of a workloads Circuit: (round_layers, round_meas, qubits) with
+    round r = layers [rl[r], rl[r+1]) then the measurements rm[r]..rm[r+1]."""
+    rl, rm, qs_ = [0], [0], []
+    cur_l, cur_m = 0, 0
+    pending = False
+    for op in circuit.ops:
+        if op[0] == "layers":
+            if op[1] != cur_l:
+                raise ValueError("layer runs must be contiguous")
+            cur_l = op[2]
+            pending = True
+        else:
+            qs_.append(np.asarray(op[1], np.uint32))
+            cur_m += len(op[1])
+            rl.append(cur_l)
+            rm.append(cur_m)
+            pending = False
+    if pending:
+        rl.append(cur_l)
+        rm.append(cur_m)
+    q = np.concatenate(qs_) if qs_ else np.zeros(0, np.uint32)
+    return np.array(rl, np.uint32), np.array(rm, np.uint32), q
+
+
+class Batch:
+    """Many circuits in one persistent launch (qs_batch_* of include/qs.h)."""
+
+    def __init__(self, circuits, seeds, shot: int = 0, device: str = "cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.circuits = list(circuits)
+        keep = []
+        arr = (qs_batch_circuit * len(self.circuits))()
+        self.meas = []
+        for i, (c, sd) in enumerate(zip(self.circuits, seeds)):
+            g = _as_gates(c.gates)
+            lp = np.ascontiguousarray(c.layer_ptr, np.int64)
+            rl, rm, q = circuit_rounds(c)
+            keep += [g, lp, rl, rm, q]
+            arr[i] = qs_batch_circuit(c.n, c.n_layers, g.ctypes.data if g.size else None,
+                                      lp.ctypes.data, len(rl) - 1, 0, rl.ctypes.data,
+                                      rm.ctypes.data, q.ctypes.data if q.size else None,
+                                      int(sd), int(shot))
+            self.meas.append(int(rm[-1]))
+        nbytes = int(lib().qs_batch_required_bytes(len(self.circuits), ctypes.byref(arr)))
+        if nbytes == 0:
+            _bcheck(-1, "qs_batch_required_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        _bcheck(lib().qs_batch_create(len(self.circuits), ctypes.byref(arr),
+                                      ctypes.c_void_p(self.stream.cuda_stream),
+                                      ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                      ctypes.byref(h)), "qs_batch_create")
+        self.h = h.value
+        self.nbytes = nbytes
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().qs_batch_destroy(ctypes.c_void_p(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, tuning: "qs_batch_tuning" = None, round_limit: int = 0):
+        _bcheck(lib().qs_batch_run(ctypes.c_void_p(self.h),
+                                   ctypes.byref(tuning) if tuning is not None else None,
+                                   round_limit), "qs_batch_run")
+
+    def sync(self):
+        _bcheck(lib().qs_batch_sync(ctypes.c_void_p(self.h)), "qs_batch_sync")
+
+    def record(self, i: int) -> np.ndarray:
+        out = np.zeros(max(self.meas[i], 1), np.uint8)
+        _bcheck(lib().qs_batch_record(ctypes.c_void_p(self.h), i, out.ctypes.data, self.meas[i]),
+                "qs_batch_record")
+        return out[:self.meas[i]]
+
+    def export_rows(self, i: int, rows):
+        n = self.circuits[i].n
+        r = np.ascontiguousarray(rows, np.uint32)
+        k = (n + 63) // 64
+        buf = np.zeros((max(len(r), 1), 2 * k + 1), np.uint64)
+        _bcheck(lib().qs_batch_export_rows(ctypes.c_void_p(self.h), i, r.ctypes.data, len(r),
+                                           buf.ctypes.data), "qs_batch_export_rows")
+        buf = buf[:len(r)]
+        bits = np.unpackbits(np.ascontiguousarray(buf[:, :2 * k]).view(np.uint8).reshape(len(r), -1),
+                             axis=1, bitorder="little")
+        return (np.ascontiguousarray(bits[:, :n]), np.ascontiguousarray(bits[:, 64 * k:64 * k + n]),
+                (buf[:, 2 * k] & 1).astype(np.uint8))
+
+    def autotune(self, round_limit: int = 0, cache_path: Optional[str] = None) -> "qs_batch_tuning":
+        t = qs_batch_tuning()
+        _bcheck(lib().qs_batch_autotune(ctypes.c_void_p(self.h), round_limit,
+                                        cache_path.encode() if cache_path else None,
+                                        ctypes.byref(t)), "qs_batch_autotune")
+        return t

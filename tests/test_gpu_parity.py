@@ -267,3 +267,34 @@ def test_full_180k_measure_twice_and_inverse():
             want_z[row - n] = 1
         assert np.array_equal(x[i], want_x) and np.array_equal(z[i], want_z) and r[i] == 0
     sim2.sync()
+
+
+@pytest.mark.parametrize("n", [1, 64, 65, 300, 2000, 14080, 14081])
+def test_fused_segments_match_per_layer_kernels(n):
+    """Device-resident layers run through the fused shared-memory kernel when
+    16 n bytes fit (n <= 14,080); with QS_FLAG_NO_FUSION every layer is its own
+    kernel. Tableau, record and frame samples must agree bit for bit."""
+    circ = C.gate_mix_circuit(n, 12, seed=n + 5, measure_every=6, measure_frac=0.05)
+    out = []
+    for flags in (0, qs.QS_FLAG_NO_FUSION):
+        s = _sim(n, flags=flags)
+        dc = s.upload(circ)
+        rec = s.run(circ, seed=3, dc=dc)
+        words = s.sample(100, seed=9, on_device=False)
+        out.append((rec, s.export(), words))
+        s.sync()
+    assert np.array_equal(out[0][0], out[1][0])
+    for a, b in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_fused_segment_oracle_parity_long_segment():
+    """A 60-layer segment through the fused kernel against the oracle."""
+    circ = C.random_circuit(1500, 60, 0.5, seed=31, measure_every=30, measure_frac=0.1)
+    sim = _sim(circ.n)
+    dc = sim.upload(circ)
+    rec = sim.run(circ, seed=8, dc=dc)
+    o, orec, _ = O.run_circuit(circ, seed=8)
+    assert np.array_equal(rec, orec)
+    _assert_tableau(sim, o)
