@@ -1,0 +1,65 @@
+"""Host-side admission logic of the server (no GPU): FIFO admission by free
+slots and a device-memory budget, concurrency bounded by both, oversize
+requests rejected, every request completed exactly once."""
+import threading
+import time
+
+import pytest
+
+from paper_2603_14641_gb300.serve import Request, Result, Scheduler
+
+
+def _fake(delay_of):
+    lock = threading.Lock()
+    log = []
+
+    def execute(req, slot, admit, fp):
+        with lock:
+            log.append(("start", req.rid, slot, admit))
+        time.sleep(delay_of(req))
+        return Result(req.rid, 0, req.shots, req.arrival_s, admit, 0.0, fp)
+
+    return execute, log
+
+
+def _reqs(sizes, gap=0.0):
+    return [Request(i, i * gap, None, shots=s, seed=i) for i, s in enumerate(sizes)]
+
+
+def test_budget_and_slots_bound_concurrency():
+    sizes = [30, 50, 20, 70, 10, 40, 60, 25]
+    ex, log = _fake(lambda r: 0.02)
+    sch = Scheduler(slots=3, budget_bytes=100, footprint=lambda r: r.shots, execute=ex)
+    res = sch.run(_reqs(sizes), realtime=False)
+    assert sorted(r.rid for r in res) == list(range(len(sizes)))
+    assert sch.peak_in_use <= 100
+    assert sch.peak_active <= 3
+    assert sch.peak_active >= 2  # requests overlapped
+    # FIFO: admission order is arrival order
+    starts = [rid for kind, rid, _, _ in sorted(log, key=lambda t: t[3])]
+    assert starts == sorted(starts)
+
+
+def test_head_of_line_waits_for_memory():
+    # the second request does not fit next to the first; it must wait, not be skipped
+    ex, log = _fake(lambda r: 0.05 if r.rid == 0 else 0.01)
+    sch = Scheduler(slots=4, budget_bytes=100, footprint=lambda r: r.shots, execute=ex)
+    res = sch.run(_reqs([80, 60, 10]), realtime=False)
+    by = {r.rid: r for r in res}
+    assert by[1].admit_s >= by[0].done_s - 1e-3
+    assert by[2].admit_s >= by[1].admit_s
+
+
+def test_oversize_request_is_rejected():
+    ex, _ = _fake(lambda r: 0.0)
+    sch = Scheduler(slots=2, budget_bytes=50, footprint=lambda r: r.shots, execute=ex)
+    with pytest.raises(MemoryError):
+        sch.run(_reqs([10, 500, 10]), realtime=False)
+
+
+def test_realtime_arrivals_are_respected():
+    ex, _ = _fake(lambda r: 0.0)
+    sch = Scheduler(slots=2, budget_bytes=1000, footprint=lambda r: r.shots, execute=ex)
+    res = sch.run(_reqs([1, 1, 1], gap=0.05), realtime=True)
+    for r in res:
+        assert r.admit_s >= r.arrival_s - 1e-3
