@@ -78,6 +78,10 @@ typedef struct qs_options {
  * instead of fusing a run of layers into one shared-memory pass (the fused
  * pass is used for n <= 14,080; results are identical either way). */
 #define QS_FLAG_NO_FUSION 1u
+/* qs_options.flags: run every measurement as five separate launches (gather,
+ * rowsum, deterministic partials, combine, finalize) instead of the pipelined
+ * two launches per measurement; results are identical either way. */
+#define QS_FLAG_UNPIPELINED_MEASURE 2u
 
 typedef struct qs_sim qs_sim;
 

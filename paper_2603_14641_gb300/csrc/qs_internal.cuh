@@ -119,6 +119,11 @@ cudaError_t launch_frame_measure(uint64_t *FX, uint64_t *FZ, uint32_t n, uint32_
                                  const uint8_t *ref, uint64_t *out, uint64_t shots, uint64_t seed,
                                  uint32_t *err, cudaStream_t s);
 cudaError_t launch_reset_meas_state(const Dev &d, cudaStream_t s);
+// a window of measurements qubits[0..count) with record indices m0.., two
+// launches per measurement (plus two per window)
+bool measure_window_supported(const Layout &L);
+cudaError_t launch_measure_window(const Dev &d, const uint32_t *qubits, uint32_t count,
+                                  uint64_t m0, qs_key key, cudaStream_t s, int *launches);
 // fused segment of L layers on a word-sliced, shared-memory-resident tableau
 // (S == nullptr: frames, no signs); lptr: L + 1 device gate offsets
 bool fused_fits(uint32_t n);

@@ -421,6 +421,12 @@ int qs_sim_apply_layers_dev(qs_sim *s, const uint32_t *packed_dev, const int64_t
 }
 
 static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint64_t m0, qs_key key) {
+  if (!(s->flags & QS_FLAG_UNPIPELINED_MEASURE) && measure_window_supported(s->d.L)) {
+    int l = 0;
+    QS_CUDA(s, launch_measure_window(s->d, qdev, count, m0, key, s->stream, &l));
+    s->launches += (uint64_t)l;
+    return QS_OK;
+  }
   for (uint32_t i = 0; i < count; ++i) {
     int l = 0;
     QS_CUDA(s, launch_measure_one(s->d, qdev, i, m0 + i, key, s->stream, &l));

@@ -298,3 +298,32 @@ def test_fused_segment_oracle_parity_long_segment():
     o, orec, _ = O.run_circuit(circ, seed=8)
     assert np.array_equal(rec, orec)
     _assert_tableau(sim, o)
+
+
+@pytest.mark.parametrize("n", [1, 3, 65, 700, 3000, 40000])
+def test_pipelined_measurements_match_five_launch_path(n):
+    """Two launches per measurement (update; finalize + next gather) against
+    the five-launch path, including repeated qubits (deterministic outcomes)
+    and a pivot row whose destabilizer partner is measured next."""
+    depth = 6 if n > 5000 else 14
+    circ = C.random_circuit(n, depth, 0.5, seed=n + 11, final_measure_all=False)
+    rng = np.random.default_rng(n)
+    q = rng.integers(0, n, size=min(3 * n, 60)).astype(np.uint32)
+    q = np.concatenate([q, q[::-1], np.arange(min(n, 40), dtype=np.uint32)])
+    outs = []
+    for flags in (0, qs.QS_FLAG_UNPIPELINED_MEASURE):
+        s = _sim(n, flags=flags)
+        dc = s.upload(circ)
+        s.apply_layers_dev(dc, 0, depth)
+        rec = s.measure(q, seed=19, shot=4)
+        rows = np.unique(np.linspace(0, 2 * n - 1, num=min(2 * n, 64)).astype(np.uint32))
+        outs.append((rec, s.export_rows(rows)))
+        s.sync()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for a, b in zip(outs[0][1], outs[1][1]):
+        assert np.array_equal(a, b)
+    if n <= 3000:
+        o = O.Oracle(n)
+        o.apply(circ.gates)
+        orec, _ = o.measure(q, seed=19, shot=4)
+        assert np.array_equal(outs[0][0], orec)
