@@ -82,6 +82,11 @@ typedef struct qs_options {
  * rowsum, deterministic partials, combine, finalize) instead of the pipelined
  * two launches per measurement; results are identical either way. */
 #define QS_FLAG_UNPIPELINED_MEASURE 2u
+/* qs_options.flags: never measure in blocks. By default a window of >= 16
+ * measurements on >= 1024 qubits is measured in blocks of up to 64 with one
+ * pass over the tableau per block (identical results); the blocked path waits
+ * for the stream once per block. */
+#define QS_FLAG_NO_BLOCKED_MEASURE 4u
 
 typedef struct qs_sim qs_sim;
 

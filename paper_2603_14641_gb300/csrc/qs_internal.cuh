@@ -124,6 +124,12 @@ cudaError_t launch_reset_meas_state(const Dev &d, cudaStream_t s);
 bool measure_window_supported(const Layout &L);
 cudaError_t launch_measure_window(const Dev &d, const uint32_t *qubits, uint32_t count,
                                   uint64_t m0, qs_key key, cudaStream_t s, int *launches);
+// blocked measurement of up to 64 qubits (scratch of blocked_scratch_bytes);
+// *len_dev receives the device address of the count actually measured
+size_t blocked_scratch_bytes(const Layout &L);
+cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qubits, int B,
+                                 uint64_t m0, qs_key key, cudaStream_t s, int *launches,
+                                 int32_t **len_dev);
 // fused segment of L layers on a word-sliced, shared-memory-resident tableau
 // (S == nullptr: frames, no signs); lptr: L + 1 device gate offsets
 bool fused_fits(uint32_t n);

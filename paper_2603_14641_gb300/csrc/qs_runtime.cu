@@ -42,6 +42,8 @@ struct Op {
 };
 
 constexpr int kRing = 4;
+constexpr uint32_t kBlockedMinCount = 16;    // windows this long use blocked measurement
+constexpr uint32_t kBlockedMinQubits = 1024;
 constexpr uint32_t kMaxQubits = 1u << 20;
 
 struct Carve {
@@ -54,7 +56,7 @@ struct Carve {
 };
 
 struct Plan {
-  size_t X, Z, RX, RZ, S, colx, mst, detx, detz, dets, err, record, stage, total;
+  size_t X, Z, RX, RZ, S, colx, mst, detx, detz, dets, err, record, stage, blk, total;
   uint64_t record_cap;
   size_t stage_bytes;
 };
@@ -78,6 +80,7 @@ Plan make_plan(const Layout &L, const qs_options *opt) {
   p.err = c.take(4);
   p.record = c.take(p.record_cap);
   p.stage = c.take(p.stage_bytes);
+  p.blk = c.take(blocked_scratch_bytes(L));
   p.total = c.off;
   return p;
 }
@@ -105,6 +108,7 @@ struct qs_sim {
   uint32_t stamp_id = 0;
   uint64_t launches = 0;
   uint32_t flags = 0;
+  void *blk = nullptr;  // scratch of the blocked measurement
 };
 
 namespace {
@@ -291,6 +295,7 @@ int qs_sim_create(uint32_t n, const qs_options *opt, void *cuda_stream, void *wo
   s->d.record = b + p.record;
   s->d.record_cap = p.record_cap;
   s->dstage = b + p.stage;
+  s->blk = b + p.blk;
   int dev = 0;
   cudaGetDevice(&dev);
   s->d.sms = 152;
@@ -421,6 +426,31 @@ int qs_sim_apply_layers_dev(qs_sim *s, const uint32_t *packed_dev, const int64_t
 }
 
 static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint64_t m0, qs_key key) {
+  if (!(s->flags & (QS_FLAG_UNPIPELINED_MEASURE | QS_FLAG_NO_BLOCKED_MEASURE)) &&
+      measure_window_supported(s->d.L) && count >= kBlockedMinCount && s->d.L.n >= kBlockedMinQubits) {
+    // blocks of up to 64 measurements; a block stops before a deterministic
+    // outcome, which then goes through the single-measurement path
+    uint32_t i = 0;
+    while (i < count) {
+      const int B = (int)std::min<uint32_t>(64, count - i);
+      int l = 0;
+      int32_t *len_dev = nullptr;
+      QS_CUDA(s, launch_measure_block(s->d, s->blk, qdev + i, B, m0 + i, key, s->stream, &l, &len_dev));
+      s->launches += (uint64_t)l;
+      int32_t done = 0;
+      QS_CUDA(s, cudaMemcpyAsync(&done, len_dev, 4, cudaMemcpyDeviceToHost, s->stream));
+      QS_CUDA(s, cudaStreamSynchronize(s->stream));
+      if (done < 0 || done > B) return fail(QS_ERR_INTERNAL, "blocked measurement length");
+      i += (uint32_t)done;
+      if (done < B) {
+        l = 0;
+        QS_CUDA(s, launch_measure_window(s->d, qdev + i, 1, m0 + i, key, s->stream, &l));
+        s->launches += (uint64_t)l;
+        i += 1;
+      }
+    }
+    return QS_OK;
+  }
   if (!(s->flags & QS_FLAG_UNPIPELINED_MEASURE) && measure_window_supported(s->d.L)) {
     int l = 0;
     QS_CUDA(s, launch_measure_window(s->d, qdev, count, m0, key, s->stream, &l));

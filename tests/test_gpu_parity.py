@@ -327,3 +327,45 @@ def test_pipelined_measurements_match_five_launch_path(n):
         o.apply(circ.gates)
         orec, _ = o.measure(q, seed=19, shot=4)
         assert np.array_equal(outs[0][0], orec)
+
+
+@pytest.mark.parametrize("n,count", [(1024, 16), (1100, 200), (2000, 150), (4097, 70)])
+def test_blocked_measurement_matches_oracle(n, count):
+    """Windows of >= 16 measurements on >= 1024 qubits go through the blocked
+    path (up to 64 measurements per tableau pass); repeated qubits force
+    deterministic outcomes that end a block early."""
+    circ = C.random_circuit(n, 12, 0.5, seed=n + count, final_measure_all=False)
+    rng = np.random.default_rng(count)
+    q = rng.permutation(n)[:count].astype(np.uint32)
+    q = np.concatenate([q[: count // 2], q[: 7], q[count // 2:]])  # repeats inside the window
+    sim = _sim(n)
+    dc = sim.upload(circ)
+    sim.apply_layers_dev(dc, 0, circ.n_layers)
+    rec = sim.measure(q, seed=23, shot=1)
+    o = O.Oracle(n)
+    o.apply(circ.gates)
+    orec, kinds = o.measure(q, seed=23, shot=1)
+    assert (kinds == 0).sum() >= 7
+    assert np.array_equal(rec, orec)
+    _assert_tableau(sim, o)
+    sim.sync()
+
+
+@pytest.mark.parametrize("n", [1500, 40000])
+def test_blocked_matches_unblocked(n):
+    depth = 8
+    circ = C.random_circuit(n, depth, 0.5, seed=7, final_measure_all=False)
+    q = np.concatenate([np.arange(0, 150, dtype=np.uint32), np.arange(0, 20, dtype=np.uint32),
+                        np.arange(n - 90, n, dtype=np.uint32)])
+    outs = []
+    for flags in (0, qs.QS_FLAG_NO_BLOCKED_MEASURE):
+        s = _sim(n, flags=flags)
+        dc = s.upload(circ)
+        s.apply_layers_dev(dc, 0, depth)
+        rec = s.measure(q, seed=5)
+        rows = np.unique(np.linspace(0, 2 * n - 1, num=200).astype(np.uint32))
+        outs.append((rec, s.export_rows(rows)))
+        s.sync()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for a, b in zip(outs[0][1], outs[1][1]):
+        assert np.array_equal(a, b)
