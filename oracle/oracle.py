@@ -41,43 +41,48 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def load_library(path: str):
+    """ctypes handle of an oracle library at `path` with its signatures set."""
+    L = ctypes.CDLL(path)
+    L.oracle_new.restype = ctypes.c_void_p
+    L.oracle_new.argtypes = [ctypes.c_int]
+    L.oracle_free.argtypes = [ctypes.c_void_p]
+    L.oracle_reset.argtypes = [ctypes.c_void_p, _u8p]
+    L.oracle_get.argtypes = [ctypes.c_void_p, _u8p, _u8p, _u8p]
+    L.oracle_set.argtypes = [ctypes.c_void_p, _u8p, _u8p, _u8p]
+    L.oracle_gate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.oracle_apply.argtypes = [ctypes.c_void_p, _u32p, ctypes.c_long]
+    L.oracle_measure.restype = ctypes.c_int
+    L.oracle_measure.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                 ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
+    L.oracle_measure_many.argtypes = [ctypes.c_void_p, _u32p, ctypes.c_long, ctypes.c_uint64,
+                                      ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _u8p,
+                                      _u8p]
+    L.oracle_odd_phase_count.restype = ctypes.c_long
+    L.oracle_odd_phase_count.argtypes = [ctypes.c_void_p]
+    L.oracle_det_check_fail.restype = ctypes.c_long
+    L.oracle_det_check_fail.argtypes = [ctypes.c_void_p]
+    L.oracle_last_kind.restype = ctypes.c_int
+    L.oracle_last_kind.argtypes = [ctypes.c_void_p]
+    L.oracle_new_subset.restype = ctypes.c_void_p
+    L.oracle_new_subset.argtypes = [ctypes.c_int, _u32p, ctypes.c_int]
+    L.oracle_get_subset.argtypes = [ctypes.c_void_p, _u8p, _u8p, _u8p]
+    L.oracle_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
+    L.oracle_coin.restype = ctypes.c_int
+    L.oracle_coin.argtypes = [ctypes.c_uint64] * 3
+    L.oracle_frame_word.restype = ctypes.c_uint64
+    L.oracle_frame_word.argtypes = [ctypes.c_uint64] * 4
+    L.oracle_frames.restype = ctypes.c_int
+    L.oracle_frames.argtypes = [ctypes.c_int, _u32p, _u32p, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                                ctypes.c_long, _u8p, ctypes.c_long, ctypes.c_uint64, _u8p]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
-        L.oracle_new.restype = ctypes.c_void_p
-        L.oracle_new.argtypes = [ctypes.c_int]
-        L.oracle_free.argtypes = [ctypes.c_void_p]
-        L.oracle_reset.argtypes = [ctypes.c_void_p, _u8p]
-        L.oracle_get.argtypes = [ctypes.c_void_p, _u8p, _u8p, _u8p]
-        L.oracle_set.argtypes = [ctypes.c_void_p, _u8p, _u8p, _u8p]
-        L.oracle_gate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
-        L.oracle_apply.argtypes = [ctypes.c_void_p, _u32p, ctypes.c_long]
-        L.oracle_measure.restype = ctypes.c_int
-        L.oracle_measure.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
-                                     ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int]
-        L.oracle_measure_many.argtypes = [ctypes.c_void_p, _u32p, ctypes.c_long, ctypes.c_uint64,
-                                          ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, _u8p,
-                                          _u8p]
-        L.oracle_odd_phase_count.restype = ctypes.c_long
-        L.oracle_odd_phase_count.argtypes = [ctypes.c_void_p]
-        L.oracle_det_check_fail.restype = ctypes.c_long
-        L.oracle_det_check_fail.argtypes = [ctypes.c_void_p]
-        L.oracle_last_kind.restype = ctypes.c_int
-        L.oracle_last_kind.argtypes = [ctypes.c_void_p]
-        L.oracle_new_subset.restype = ctypes.c_void_p
-        L.oracle_new_subset.argtypes = [ctypes.c_int, _u32p, ctypes.c_int]
-        L.oracle_get_subset.argtypes = [ctypes.c_void_p, _u8p, _u8p, _u8p]
-        L.oracle_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
-        L.oracle_coin.restype = ctypes.c_int
-        L.oracle_coin.argtypes = [ctypes.c_uint64] * 3
-        L.oracle_frame_word.restype = ctypes.c_uint64
-        L.oracle_frame_word.argtypes = [ctypes.c_uint64] * 4
-        L.oracle_frames.restype = ctypes.c_int
-        L.oracle_frames.argtypes = [ctypes.c_int, _u32p, _u32p, ctypes.POINTER(ctypes.c_int),
-                                    ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
-                                    ctypes.c_long, _u8p, ctypes.c_long, ctypes.c_uint64, _u8p]
-        _lib = L
+        _lib = load_library(build())
     return _lib
 
 

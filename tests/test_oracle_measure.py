@@ -152,3 +152,47 @@ def test_deterministic_product_order_independent():
             assert kind[0] == 0 and got[0] == want
             checked += 1
     assert checked > 0
+
+
+def test_rowsum_against_pauli_product_table():
+    """Every row the probabilistic update rewrites equals S_p * row (with sign)
+    computed by an independent 2x2 Pauli multiplication table (the rowsum of
+    Aaronson & Gottesman cited in Sec. 2.5); D_{p-n} = S_p; S_p = +-Z_q."""
+    checked = 0
+    for trial in range(120):
+        n = 3 + trial % 5
+        circ = C.gate_mix_circuit(n, 8 + trial % 7, 1000 + trial, final_measure_all=False)
+        o = O.Oracle(n)
+        o.apply(circ.gates)
+        x, z, r = o.get()
+        for q in range(n):
+            if not x[n:, q].any():
+                continue
+            p = n + int(np.argmax(x[n:, q]))
+            o2 = O.Oracle(n)
+            o2.set(x, z, r)
+            out, kind = o2.measure([q], seed=trial, shot=q)
+            assert kind[0] == 1
+            x2, z2, r2 = o2.get()
+            for h in range(2 * n):
+                if h in (p, p - n):
+                    continue
+                if x[h, q]:
+                    ex, ez, ph = SV.pauli_product(x[p], z[p], r[p], x[h], z[h], r[h])
+                    assert ph in (0, 2)
+                    assert np.array_equal(x2[h], ex) and np.array_equal(z2[h], ez)
+                    assert r2[h] == ph // 2
+                    checked += 1
+                else:
+                    assert np.array_equal(x2[h], x[h]) and r2[h] == r[h]
+            assert np.array_equal(x2[p - n], x[p]) and r2[p - n] == r[p]
+            assert not x2[p].any() and z2[p].sum() == 1 and z2[p, q] == 1 and r2[p] == out[0]
+            break
+    assert checked > 150
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_measurement_against_state_vector_many_seeds(seed):
+    n = 2 + seed % 7
+    circ = C.gate_mix_circuit(n, 14, 500 + seed, measure_every=3, measure_frac=0.6)
+    _sv_check_circuit(circ, seed=seed)

@@ -1,0 +1,118 @@
+"""The oracle's pins catch plausible mistakes (no GPU).
+
+(Multiplying the rowsum operands in the other order is not a mistake: the
+rows it multiplies commute, so that mutant is equivalent and not listed.)
+
+Each case compiles a copy of oracle/chp_oracle.c with one planted mistake --
+a dropped term, a wrong sign, a transposed operand, the wrong rows -- loads it
+in place of the oracle and checks that at least one pin of
+tests/test_oracle_*.py now fails. The oracle's own source is not touched.
+"""
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+from oracle import oracle as O
+from tests import test_oracle_frames as TF
+from tests import test_oracle_gates as TG
+from tests import test_oracle_measure as TM
+from workloads import circuits as C
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                   "chp_oracle.c")
+
+
+def _pins_gates():
+    for g in (C.X, C.Y, C.Z, C.H, C.S, C.SDG):
+        TG.test_one_qubit_rules_match_conjugation(g)
+    for g in (C.CX, C.CY, C.CZ, C.SWAP, C.ISWAP):
+        TG.test_two_qubit_rules_match_conjugation(g, 0, 1)
+        TG.test_two_qubit_rules_match_conjugation(g, 1, 0)
+
+
+def _pins_measure():
+    TM.test_rowsum_against_pauli_product_table()
+    for n, seed in [(3, 3), (5, 4), (8, 6)]:
+        TM.test_measurement_against_state_vector(n, seed)
+    TM.test_bell_and_ghz_closed_forms()
+    TM.test_invariants_after_measurements()
+    TM.test_deterministic_product_order_independent()
+
+
+def _pins_philox():
+    TM.test_philox_matches_numpy((5, 7, 9, 11), (3, 0x51A7E))
+    TM.test_coin_and_frame_word_definitions()
+
+
+def _pins_frames():
+    TF.test_frames_support_and_distribution(5, 2, 3, 0.4)
+    TF.test_frames_support_and_distribution(6, 3, 4, 0.5)
+    TF.test_frames_reference_is_deterministic_part()
+
+
+MUTATIONS = [
+    ("CX sign drops the negation",
+     "t->r[i] ^= (uint8_t)(xc & zt & ((xt ^ zc) ^ 1u));",
+     "t->r[i] ^= (uint8_t)(xc & zt & (xt ^ zc));", _pins_gates),
+    ("H forgets the sign",
+     "    t->r[i] ^= (uint8_t)(x & z);\n    XB(t, i, q) = z;",
+     "    XB(t, i, q) = z;", _pins_gates),
+    ("CX updates the wrong z column",
+     "ZB(t, i, c) = (uint8_t)(zc ^ zt);", "ZB(t, i, tq) = (uint8_t)(zt ^ zc);", _pins_gates),
+    ("Pauli Z flips on z instead of x",
+     "case G_Z: rule_pauli(t, a, 0, 1); break;", "case G_Z: rule_pauli(t, a, 1, 0); break;",
+     _pins_gates),
+    ("g function: wrong sign for X * .",
+     "return z2 * (2 * x2 - 1); /* X * . */", "return z2 * (1 - 2 * x2); /* X * . */",
+     _pins_measure),
+    ("rowsum drops 2 r_i",
+     "long sum = 2 * (long)t->r[h] + 2 * (long)t->r[i];", "long sum = 2 * (long)t->r[h];",
+     _pins_measure),
+    ("rowsum transposes x and z of the target",
+     "sum += g_fn(XB(t, i, j), ZB(t, i, j), XB(t, h, j), ZB(t, h, j));",
+     "sum += g_fn(XB(t, i, j), ZB(t, i, j), ZB(t, h, j), XB(t, h, j));", _pins_measure),
+    ("deterministic product uses destabilizers",
+     "if (XB(t, i, q)) rowsum(t, s, i + n);", "if (XB(t, i, q)) rowsum(t, s, i);", _pins_measure),
+    ("pivot searched among destabilizers",
+     "for (int i = n; i < 2 * n; ++i)\n    if (XB(t, i, q)) { p = i; break; }",
+     "for (int i = 0; i < n; ++i)\n    if (XB(t, i, q)) { p = i + n; break; }", _pins_measure),
+    ("D_{p-n} not replaced by S_p",
+     "memcpy(&XB(t, p - n, 0), &XB(t, p, 0), (size_t)n);", ";", _pins_measure),
+    ("Philox Weyl constant wrong",
+     "k0 += 0x9E3779B97F4A7C15ull;", "k0 += 0x9E3779B97F4A7C16ull;", _pins_philox),
+    ("coin reads word 1",
+     "return (int)(out[0] & 1u);", "return (int)(out[1] & 1u);", _pins_philox),
+    ("frames forget the re-randomisation after a measurement",
+     "fz[q] = (uint8_t)((oracle_frame_word(seed, (uint64_t)m + 1, (uint64_t)q, j) >> bit) & 1u);",
+     ";", _pins_frames),
+    ("frames drop the reference record",
+     "(uint8_t)(fx[q] ^ ref[m]);", "(uint8_t)(fx[q]);", _pins_frames),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(name, old, new, pins):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found once: {old!r}"
+    mutant = src.replace(old, new)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "mutant.c")
+        so = os.path.join(d, "mutant.so")
+        open(c, "w").write(mutant)
+        subprocess.check_call(["gcc", "-O1", "-std=c99", "-shared", "-fPIC", "-o", so, c])
+        saved = O._lib
+        O._lib = O.load_library(so)
+        try:
+            with pytest.raises(AssertionError):
+                pins()
+        finally:
+            O._lib = saved
+
+
+def test_unmutated_oracle_passes_the_same_pins():
+    _pins_gates()
+    _pins_measure()
+    _pins_philox()
+    _pins_frames()
