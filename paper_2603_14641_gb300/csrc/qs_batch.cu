@@ -43,6 +43,7 @@ constexpr uint32_t kBatchMaxQubits = 8192;  // det partials: <= 4 words per lane
 
 struct BCirc {
   uint32_t n, k, cs, rs, ncols, nrows;
+  uint32_t lpr, pad_;  // lanes per row in the update phase (power of two <= 32)
   uint64_t *X, *Z, *S, *RX, *RZ;
   uint32_t *colx;
   int64_t *mst;
@@ -60,6 +61,7 @@ struct BAct {
   uint64_t m0;    // record index of the round's first measurement
   uint64_t pre;   // exclusive prefix of the list's items (slices / tiles)
   uint64_t pre2;  // exclusive prefix of rows (measurement list)
+  uint64_t pre3;  // exclusive prefix of warp units (32 / lpr rows each) in the update phase
 };
 
 struct BRound {
@@ -111,11 +113,11 @@ __device__ bool grid_sync(const BProg &P) {
 
 // entry of a list [first, first + count) holding flattened index i
 __device__ __forceinline__ uint32_t find_act(const BAct *a, uint32_t first, uint32_t count,
-                                             uint64_t i, bool rows) {
+                                             uint64_t i, int key) {
   uint32_t lo = 0, hi = count;
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) >> 1;
-    const uint64_t v = rows ? a[first + mid].pre2 : a[first + mid].pre;
+    const uint64_t v = key == 2 ? a[first + mid].pre3 : (key == 1 ? a[first + mid].pre2 : a[first + mid].pre);
     if (v <= i) lo = mid; else hi = mid;
   }
   return first + lo;
@@ -180,7 +182,7 @@ __device__ void phase_transpose(const BProg &P, const BRound &R, bool to_rows, u
   uint64_t(*tile)[5] = reinterpret_cast<uint64_t(*)[5]>(smem + (size_t)gid * 256 * 5);
   const uint64_t total = P.acts[R.m_first + R.m_count].pre;
   for (uint64_t t = (uint64_t)blockIdx.x * groups + gid; t < total; t += (uint64_t)gridDim.x * groups) {
-    const BAct &A = P.acts[find_act(P.acts, R.m_first, R.m_count, t, false)];
+    const BAct &A = P.acts[find_act(P.acts, R.m_first, R.m_count, t, 0)];
     const BCirc &C = P.circs[A.c];
     const uint64_t per = (uint64_t)(C.cs / 4) * (C.ncols / 256);
     const uint64_t tt = t - A.pre;
@@ -202,7 +204,7 @@ __device__ void phase_gates(const BProg &P, const BRound &R, uint64_t *smem) {
   const uint64_t total = P.acts[R.g_first + R.g_count].pre;
   const uint32_t W = P.wpb;
   for (uint64_t it = blockIdx.x; it < total; it += gridDim.x) {
-    const BAct &A = P.acts[find_act(P.acts, R.g_first, R.g_count, it, false)];
+    const BAct &A = P.acts[find_act(P.acts, R.g_first, R.g_count, it, 0)];
     const BCirc &C = P.circs[A.c];
     const uint32_t n = C.n, w0 = (uint32_t)(it - A.pre) * W;
     uint64_t *sx = smem, *sz = smem + (size_t)n * W;
@@ -273,19 +275,35 @@ __device__ __forceinline__ uint32_t active_count(const BProg &P, const BRound &R
   return lo;
 }
 
+// contiguous range [*b, *e) of `total` items for the calling warp
+__device__ __forceinline__ void warp_range(uint64_t total, uint64_t *b, uint64_t *e) {
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t per = (total + nw - 1) / nw;
+  *b = min(total, w * per);
+  *e = min(total, *b + per);
+}
+
 __device__ void phase_gather(const BProg &P, const BRound &R, uint32_t j, uint32_t a) {
-  const uint64_t total = P.acts[R.m_first + a].pre2;
-  const uint64_t gt = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = gt; i < total; i += nt) {
-    const BAct &A = P.acts[find_act(P.acts, R.m_first, a, i, true)];
+  // a warp takes a contiguous run of 32-row groups; circuits are found once
+  // per run and then followed linearly
+  const uint64_t groups = P.acts[R.m_first + a].pre2 >> 5;
+  uint64_t g0, g1;
+  warp_range(groups, &g0, &g1);
+  if (g0 >= g1) return;
+  const int lane = threadIdx.x & 31;
+  uint32_t e = find_act(P.acts, R.m_first, a, g0 << 5, 1);
+  for (uint64_t g = g0; g < g1; ++g) {
+    const uint64_t i = g << 5;
+    while (e + 1 < R.m_first + a && P.acts[e + 1].pre2 <= i) ++e;
+    const BAct &A = P.acts[e];
     const BCirc &C = P.circs[A.c];
-    const uint32_t r = (uint32_t)(i - A.pre2);
+    const uint32_t r = (uint32_t)(i - A.pre2) + lane;
     const uint32_t q = C.qubits[A.q0 + j];
     uint32_t bit = 0;
     if (q < C.n) bit = (uint32_t)(C.RX[(size_t)r * C.rs + (q >> 6)] >> (q & 63)) & 1u;
     const uint32_t ball = __ballot_sync(0xffffffffu, bit);
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
       if (q >= C.n) {
         if (r == 0) atomicOr(P.err, kErrBadQubit);
         continue;
@@ -303,77 +321,90 @@ __device__ void phase_gather(const BProg &P, const BRound &R, uint32_t j, uint32
 }
 
 __device__ void phase_update(const BProg &P, const BRound &R, uint32_t j, uint32_t a) {
-  const uint64_t total = P.acts[R.m_first + a].pre2;
+  // warp units: a unit is 32 / lpr consecutive rows of one circuit, lpr lanes per row
+  const uint64_t total = P.acts[R.m_first + a].pre3;
   const int lane = threadIdx.x & 31;
-  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t i = gw; i < total; i += nw) {
-    const BAct &A = P.acts[find_act(P.acts, R.m_first, a, i, true)];
+  uint64_t u0, u1;
+  warp_range(total, &u0, &u1);
+  if (u0 >= u1) return;
+  uint32_t e = find_act(P.acts, R.m_first, a, u0, 2);
+  for (uint64_t i = u0; i < u1; ++i) {
+    while (e + 1 < R.m_first + a && P.acts[e + 1].pre3 <= i) ++e;
+    const BAct &A = P.acts[e];
     const BCirc &C = P.circs[A.c];
-    const uint32_t r = (uint32_t)(i - A.pre2);
+    const uint32_t G = C.lpr, rpw = 32 / G;
+    const uint32_t unit = (uint32_t)(i - A.pre3);
     const uint32_t q = C.qubits[A.q0 + j];
     if (q >= C.n) continue;
     const int64_t p = C.mst[kMsPivot];
     if (p != kBNoPivot) {
       const int64_t pd = p - 64ll * C.k;
-      if (((C.colx[r >> 5] >> (r & 31)) & 1u) == 0 || (int64_t)r == p || (int64_t)r == pd) continue;
-      const ulonglong2 *px = reinterpret_cast<const ulonglong2 *>(C.RX + (size_t)p * C.rs);
-      const ulonglong2 *pz = reinterpret_cast<const ulonglong2 *>(C.RZ + (size_t)p * C.rs);
-      ulonglong2 *rx = reinterpret_cast<ulonglong2 *>(C.RX + (size_t)r * C.rs);
-      ulonglong2 *rz = reinterpret_cast<ulonglong2 *>(C.RZ + (size_t)r * C.rs);
+      const uint32_t sub = lane / G, sl = lane % G;
+      const uint32_t r = unit * rpw + sub;
+      const bool tgt = r < C.nrows && ((C.colx[r >> 5] >> (r & 31)) & 1u) != 0 && (int64_t)r != p &&
+                       (int64_t)r != pd;
       int acc = 0;
-      for (uint32_t v = lane; v < C.rs / 2; v += 32) {
-        const ulonglong2 x = rx[v], z = rz[v], ax = px[v], cz = pz[v];
-        const ulonglong2 nx = make_ulonglong2(x.x ^ ax.x, x.y ^ ax.y);
-        const ulonglong2 nz = make_ulonglong2(z.x ^ cz.x, z.y ^ cz.y);
-        acc += __popcll(x.x & z.x) + __popcll(x.y & z.y);
-        acc += 2 * (__popcll(cz.x & x.x) + __popcll(cz.y & x.y));
-        acc += __popcll(ax.x & cz.x) + __popcll(ax.y & cz.y);  // |x_p & z_p| for this word
-        acc -= __popcll(nx.x & nz.x) + __popcll(nx.y & nz.y);
-        rx[v] = nx;
-        rz[v] = nz;
+      if (tgt) {
+        const ulonglong2 *px = reinterpret_cast<const ulonglong2 *>(C.RX + (size_t)p * C.rs);
+        const ulonglong2 *pz = reinterpret_cast<const ulonglong2 *>(C.RZ + (size_t)p * C.rs);
+        ulonglong2 *rx = reinterpret_cast<ulonglong2 *>(C.RX + (size_t)r * C.rs);
+        ulonglong2 *rz = reinterpret_cast<ulonglong2 *>(C.RZ + (size_t)r * C.rs);
+        for (uint32_t v = sl; v < C.rs / 2; v += G) {
+          const ulonglong2 x = rx[v], z = rz[v], ax = px[v], cz = pz[v];
+          const ulonglong2 nx = make_ulonglong2(x.x ^ ax.x, x.y ^ ax.y);
+          const ulonglong2 nz = make_ulonglong2(z.x ^ cz.x, z.y ^ cz.y);
+          acc += __popcll(x.x & z.x) + __popcll(x.y & z.y);
+          acc += 2 * (__popcll(cz.x & x.x) + __popcll(cz.y & x.y));
+          acc += __popcll(ax.x & cz.x) + __popcll(ax.y & cz.y);  // |x_p & z_p| for this word
+          acc -= __popcll(nx.x & nz.x) + __popcll(nx.y & nz.y);
+          rx[v] = nx;
+          rz[v] = nz;
+        }
       }
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) {
+      // reduction inside each group of G lanes (offsets < G never cross groups)
+      for (uint32_t o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (sl == 0 && tgt) {
         const int rp = (int)((C.S[p >> 6] >> (p & 63)) & 1u);
         const int t = bmod4(acc + 2 * rp);
         if (t & 1) atomicOr(P.err, kErrOddPhase);
         if (t >> 1) atomicXor(reinterpret_cast<unsigned long long *>(&C.S[r >> 6]), 1ull << (r & 63));
       }
-    } else if (r < C.k) {
-      // deterministic case: chunk r = destabilizer rows 64 r .. 64 r + 63
+    } else {
+      // deterministic case: chunks (64 destabilizer rows each) of this unit, whole warp per chunk
       const uint64_t *colx64 = reinterpret_cast<const uint64_t *>(C.colx);
-      uint64_t m = colx64[r];
-      uint64_t px[4] = {0, 0, 0, 0}, pz[4] = {0, 0, 0, 0}, cross = 0;
-      int cnt = 0;
-      const int rsum = __popcll(m & C.S[C.k + r]);
-      while (m) {
-        const int b = __ffsll((long long)m) - 1;
-        m &= m - 1;
-        const size_t row = 64ull * C.k + 64ull * r + b;
+      for (uint32_t r = unit * rpw; r < (unit + 1) * rpw && r < C.k; ++r) {
+        uint64_t m = colx64[r];
+        uint64_t px[4] = {0, 0, 0, 0}, pz[4] = {0, 0, 0, 0}, cross = 0;
+        int cnt = 0;
+        const int rsum = __popcll(m & C.S[C.k + r]);
+        while (m) {
+          const int b = __ffsll((long long)m) - 1;
+          m &= m - 1;
+          const size_t row = 64ull * C.k + 64ull * r + b;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const uint32_t u = lane + 32 * t;
+            if (u < C.k) {
+              const uint64_t x = C.RX[row * C.rs + u], z = C.RZ[row * C.rs + u];
+              cross ^= x & pz[t];
+              cnt += __popcll(x & z);
+              px[t] ^= x;
+              pz[t] ^= z;
+            }
+          }
+        }
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const uint32_t u = lane + 32 * t;
           if (u < C.k) {
-            const uint64_t x = C.RX[row * C.rs + u], z = C.RZ[row * C.rs + u];
-            cross ^= x & pz[t];
-            cnt += __popcll(x & z);
-            px[t] ^= x;
-            pz[t] ^= z;
+            C.det_x[(size_t)r * C.rs + u] = px[t];
+            C.det_z[(size_t)r * C.rs + u] = pz[t];
           }
         }
+        int v = cnt + 2 * (__popcll(cross) & 1);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) C.det_scal[r] = bmod4(v + 2 * rsum);
       }
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const uint32_t u = lane + 32 * t;
-        if (u < C.k) {
-          C.det_x[(size_t)r * C.rs + u] = px[t];
-          C.det_z[(size_t)r * C.rs + u] = pz[t];
-        }
-      }
-      int v = cnt + 2 * (__popcll(cross) & 1);
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) C.det_scal[r] = bmod4(v + 2 * rsum);
     }
   }
 }
@@ -654,21 +685,22 @@ static int build_acts(qs_batch *b, uint32_t wpb) {
       return (b->rm[x][r + 1] - b->rm[x][r]) > (b->rm[y][r + 1] - b->rm[y][r]);
     });
     R.m_first = (uint32_t)acts.size();
-    uint64_t pt = 0, pr = 0;
+    uint64_t pt = 0, pr = 0, pu = 0;
     R.max_qn = 0;
     for (uint32_t c : mc) {
       BAct a{};
       a.c = c; a.q0 = b->rm[c][r]; a.qn = b->rm[c][r + 1] - b->rm[c][r];
       a.m0 = a.q0;
-      a.pre = pt; a.pre2 = pr;
+      a.pre = pt; a.pre2 = pr; a.pre3 = pu;
       acts.push_back(a);
       const BCirc &C = b->circs[c];
       pt += 2ull * (C.cs / 4) * (C.ncols / 256);
       pr += C.nrows;
+      pu += C.nrows / (32 / C.lpr);
       R.max_qn = std::max(R.max_qn, a.qn);
     }
     R.m_count = (uint32_t)mc.size();
-    { BAct s{}; s.pre = pt; s.pre2 = pr; acts.push_back(s); }
+    { BAct s{}; s.pre = pt; s.pre2 = pr; s.pre3 = pu; acts.push_back(s); }
     rounds[r] = R;
   }
   if (acts.size() > b->acts_cap) return bfail(QS_ERR_INTERNAL, "work list capacity");
@@ -738,6 +770,8 @@ int qs_batch_create(uint32_t count, const qs_batch_circuit *cc, void *stream, vo
     BCirc C{};
     C.n = c.n;
     layout_of(c.n, C.k, C.cs, C.ncols, C.rs, C.nrows);
+    C.lpr = 1;
+    while (C.lpr < 32 && C.lpr < C.rs / 2) C.lpr <<= 1;
     C.X = reinterpret_cast<uint64_t *>(base + P.off_X[i]);
     C.Z = reinterpret_cast<uint64_t *>(base + P.off_Z[i]);
     C.S = reinterpret_cast<uint64_t *>(base + P.off_S[i]);
