@@ -48,7 +48,8 @@ extern "C" {
 /* Gate types: the paper's 11-gate Clifford set (Sec. 6 "Benchmarks") plus identity. */
 enum {
   QS_I = 0, QS_X = 1, QS_Y = 2, QS_Z = 3, QS_H = 4, QS_S = 5, QS_SDG = 6,
-  QS_CX = 7, QS_CY = 8, QS_CZ = 9, QS_SWAP = 10, QS_ISWAP = 11, QS_NUM_GATE_TYPES = 12
+  QS_CX = 7, QS_CY = 8, QS_CZ = 9, QS_SWAP = 10, QS_ISWAP = 11, QS_NUM_GATE_TYPES = 12,
+  QS_MEASURE = 12 /* operation type of qs_schedule_windows only: Z-measurement of q0 */
 };
 
 /* One gate record. q1 is ignored for one-qubit gates; for CX/CY q0 is the
@@ -340,6 +341,26 @@ int qs_batch_autotune(qs_batch *batch, uint32_t round_limit, const char *cache_p
 
 /* Message for the last batch error on the calling thread. */
 const char *qs_batch_last_error(void);
+
+/*
+ * Window scheduling (Sec. 4.2, ScheduleWindows of Alg. 2) of an ordered list of
+ * gates and measurements (type QS_MEASURE) on n qubits. Repeatedly: every gate
+ * that is the first remaining operation on all its qubits forms one window of
+ * parallel gates (a layer); then every measurement that has become first on its
+ * qubit is emitted in ascending qubit order, each as its own window, or all as
+ * one window when merge_measurements (the paper's sampling mode). Dependencies
+ * on each qubit are kept; this reproduces the worked example of Sec. 4.2.
+ *   out_ops:         count reordered operations
+ *   out_window_ptr:  count + 1 offsets; window w = out_ops[ptr[w] .. ptr[w+1])
+ *   out_window_kind: count entries, 0 = gates, 1 = measurements
+ *   n_windows:       number of windows written
+ * Errors: QS_ERR_ARG (unknown type, qubit >= n, two-qubit gate on one qubit);
+ * message via qs_schedule_last_error().
+ */
+int qs_schedule_windows(uint32_t n, const qs_gate *ops, uint32_t count, int merge_measurements,
+                        qs_gate *out_ops, uint32_t *out_window_ptr, uint8_t *out_window_kind,
+                        uint32_t *n_windows);
+const char *qs_schedule_last_error(void);
 
 /* Number of kernel launches the sim has enqueued so far. */
 uint64_t qs_sim_launch_count(const qs_sim *sim);

@@ -23,6 +23,7 @@ ERRORS = {-1: "QS_ERR_ARG", -2: "QS_ERR_OOM", -3: "QS_ERR_CUDA", -4: "QS_ERR_TIM
 QS_LAYOUT_ROWS_PACKED = 0
 
 GATES = dict(I=0, X=1, Y=2, Z=3, H=4, S=5, SDG=6, CX=7, CY=8, CZ=9, SWAP=10, ISWAP=11)
+QS_MEASURE = 12
 
 
 class QsError(RuntimeError):
@@ -88,6 +89,9 @@ SIGNATURES = {
     "qs_sim_export_rows": (ctypes.c_int, [_vp, _vp, _u32, _vp]),
     "qs_sim_sync": (ctypes.c_int, [_vp]),
     "qs_sim_launch_count": (_u64, [_vp]),
+    "qs_schedule_windows": (ctypes.c_int, [_u32, _vp, _u32, ctypes.c_int, _vp, _vp, _vp,
+                                           ctypes.POINTER(_u32)]),
+    "qs_schedule_last_error": (ctypes.c_char_p, []),
     "qs_batch_required_bytes": (_sz, [_u32, _vp]),
     "qs_batch_create": (ctypes.c_int, [_u32, _vp, _vp, _vp, _sz, ctypes.POINTER(_vp)]),
     "qs_batch_destroy": (ctypes.c_int, [_vp]),
@@ -506,3 +510,47 @@ class Batch:
                                         cache_path.encode() if cache_path else None,
                                         ctypes.byref(t)), "qs_batch_autotune")
         return t
+
+
+# ----------------------------------------------------------------------
+# Window scheduling (Sec. 4.2)
+# ----------------------------------------------------------------------
+
+def qs_schedule_windows(n: int, ops: np.ndarray, merge_measurements: bool = False):
+    """ops: (count, 3) uint32 rows (type, q0, q1), type QS_MEASURE for a
+    Z-measurement. Returns (out_ops, window_ptr, window_kind)."""
+    o = _as_gates(ops)
+    count = o.shape[0]
+    out = np.zeros((max(count, 1), 3), np.uint32)
+    ptr = np.zeros(count + 1, np.uint32)
+    kind = np.zeros(max(count, 1), np.uint8)
+    nw = ctypes.c_uint32(0)
+    rc = lib().qs_schedule_windows(n, _ptr(o) if count else None, count, int(merge_measurements),
+                                   _ptr(out), _ptr(ptr), _ptr(kind), ctypes.byref(nw))
+    if rc != QS_OK:
+        raise QsError(rc, "qs_schedule_windows", lib().qs_schedule_last_error().decode())
+    w = nw.value
+    return out[:count], ptr[:w + 1].astype(np.int64), kind[:w]
+
+
+def scheduled_circuit(n: int, ops: np.ndarray, merge_measurements: bool = False, name: str = ""):
+    """A workloads.circuits.Circuit from an ordered op list via qs_schedule_windows:
+    gate windows become layers, measurement windows become measurement ops."""
+    from workloads.circuits import Circuit
+    out, ptr, kind = qs_schedule_windows(n, ops, merge_measurements)
+    gates, layer_ptr, prog = [], [0], []
+    for w in range(len(kind)):
+        seg = out[ptr[w]:ptr[w + 1]]
+        if kind[w] == 0:
+            gates.append(seg)
+            layer_ptr.append(layer_ptr[-1] + len(seg))
+            l = len(layer_ptr) - 2
+            if prog and prog[-1][0] == "layers" and prog[-1][2] == l:
+                prog[-1] = ("layers", prog[-1][1], l + 1)
+            else:
+                prog.append(("layers", l, l + 1))
+        else:
+            prog.append(("measure", np.ascontiguousarray(seg[:, 1], np.uint32)))
+    g = np.concatenate(gates) if gates else np.zeros((0, 3), np.uint32)
+    return Circuit(n=n, gates=np.ascontiguousarray(g, np.uint32),
+                   layer_ptr=np.array(layer_ptr, np.int64), ops=prog, name=name)

@@ -369,3 +369,34 @@ def test_blocked_matches_unblocked(n):
     assert np.array_equal(outs[0][0], outs[1][0])
     for a, b in zip(outs[0][1], outs[1][1]):
         assert np.array_equal(a, b)
+
+
+def test_qasm_front_end_end_to_end():
+    """OpenQASM text over the 11-gate set with interleaved measurements,
+    scheduled into windows (Sec. 4.2), run on the GPU against the oracle."""
+    from paper_2603_14641_gb300 import qasm
+    rng = np.random.default_rng(17)
+    n = 37
+    names1 = ["x", "y", "z", "h", "s", "sdg"]
+    names2 = ["cx", "cy", "cz", "swap", "iswap"]
+    lines = ["OPENQASM 2.0;", 'include "qelib1.inc";', f"qreg q[{n}];", f"creg c[{n}];"]
+    for _ in range(600):
+        r = rng.random()
+        if r < 0.1:
+            q = int(rng.integers(n))
+            lines.append(f"measure q[{q}] -> c[{q}];")
+        elif r < 0.5:
+            a, b = rng.choice(n, size=2, replace=False)
+            lines.append(f"{rng.choice(names2)} q[{a}],q[{b}];")
+        else:
+            lines.append(f"{rng.choice(names1)} q[{int(rng.integers(n))}];")
+    circ = qasm.load_circuit("\n".join(lines))
+    sim = _sim(circ.n)
+    rec = sim.run(circ, seed=4)
+    o, orec, _ = O.run_circuit(circ, seed=4)
+    assert len(rec) == sum(1 for l in lines if l.startswith("measure"))
+    assert np.array_equal(rec, orec)
+    _assert_tableau(sim, o)
+    words = sim.sample(100, seed=6, on_device=False)
+    bits = np.unpackbits(words.view(np.uint8), axis=1, bitorder="little")[:, :100]
+    assert np.array_equal(bits, O.frames(circ, rec, 100, seed=6))
