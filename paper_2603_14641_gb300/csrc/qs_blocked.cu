@@ -38,7 +38,7 @@ namespace qs {
 constexpr int64_t kBlkNone = LLONG_MAX;
 constexpr int32_t kBaseOrig = -1;
 constexpr int32_t kBasePivot = 1000;  // base = kBasePivot + j: pivot row of step j
-constexpr int kCW = 64;               // column words per phase-3 chunk
+constexpr int kCW = 32;               // column words per phase-3 chunk
 
 struct BlkState {
   int64_t slot[3];     // pivot search results, rotating
@@ -150,50 +150,83 @@ blk_step_kernel(uint64_t nrows, uint32_t n, uint32_t k, int j, int B, const uint
   }
 }
 
-// pivot rows V_j and the per-word phase sums; one thread per column word u
-__global__ void __launch_bounds__(128)
+// pivot rows V_j and their phase sums for one chunk of 32 column words.
+// V_j is the product of the original pivot rows p_s over a set E_j of steps:
+// E_j = {j} xor (xor of E_s over the steps s that targeted p_j before step j),
+// built by one warp in step order; every V_j of the chunk is then independent.
+// Lane = column word; warp w takes steps w, w + 16, ...
+constexpr int kVrowThreads = 512;
+constexpr size_t kVrowSmem = 4ull * 64 * 32 * sizeof(uint64_t);  // original and V rows, x and z
+
+__global__ void __launch_bounds__(kVrowThreads)
 blk_vrows_kernel(const uint64_t *__restrict__ RX, const uint64_t *__restrict__ RZ, uint32_t rs,
-                 uint32_t k, uint64_t *__restrict__ VX, uint64_t *__restrict__ VZ, BlkState *st) {
+                 uint64_t *__restrict__ VX, uint64_t *__restrict__ VZ, BlkState *st) {
+  extern __shared__ uint64_t vsm[];
+  uint64_t(*ox)[32] = reinterpret_cast<uint64_t(*)[32]>(vsm);
+  uint64_t(*oz)[32] = reinterpret_cast<uint64_t(*)[32]>(vsm + 64 * 32);
+  uint64_t(*vx)[32] = reinterpret_cast<uint64_t(*)[32]>(vsm + 2 * 64 * 32);
+  uint64_t(*vz)[32] = reinterpret_cast<uint64_t(*)[32]>(vsm + 3 * 64 * 32);
+  __shared__ uint64_t sE[64];
   const int L = st->len;
-  __shared__ int sA[64], sB[64], sC[64];
-  __shared__ unsigned long long sG[64];
-  if (threadIdx.x < 64) { sA[threadIdx.x] = 0; sB[threadIdx.x] = 0; sC[threadIdx.x] = 0; sG[threadIdx.x] = 0; }
-  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   // every word of the padded row (u < rs): padding qubit words are zero in the
-  // tableau and must come out zero from the V rows too
-  const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u < rs) {
+  // tableau and come out zero in the V rows too
+  const uint32_t u = blockIdx.x * 32 + lane;
+  const bool in = u < rs;
+  for (int j = w; j < L; j += nw) {
+    const uint64_t p = (uint64_t)st->piv[j];
+    ox[j][lane] = in ? RX[p * rs + u] : 0;
+    oz[j][lane] = in ? RZ[p * rs + u] : 0;
+  }
+  if (w == 0) {
     for (int j = 0; j < L; ++j) {
-      const int64_t p = st->piv[j];
-      const uint64_t x0 = RX[(uint64_t)p * rs + u], z0 = RZ[(uint64_t)p * rs + u];
-      uint64_t vx = x0, vz = z0, m = st->mpiv[j];
-      while (m) {
-        const int s = __ffsll((long long)m) - 1;
-        m &= m - 1;
-        vx ^= VX[(uint64_t)s * rs + u];
-        vz ^= VZ[(uint64_t)s * rs + u];
-      }
-      VX[(uint64_t)j * rs + u] = vx;
-      VZ[(uint64_t)j * rs + u] = vz;
-      const int a = __popcll(vx & vz), b = __popcll(x0 & z0), c = __popcll((vz ^ z0) & x0) & 1;
-      if (a) atomicAdd(&sA[j], a);
-      if (b) atomicAdd(&sB[j], b);
-      if (c) atomicXor(&sC[j], 1);
-    }
-    for (int s = 0; s < L; ++s) {
-      const uint64_t zs = VZ[(uint64_t)s * rs + u];
-      uint64_t row = 0;
-      for (int t = 0; t < L; ++t) row |= (uint64_t)(__popcll(zs & VX[(uint64_t)t * rs + u]) & 1) << t;
-      if (row) atomicXor(&sG[s], (unsigned long long)row);
+      const uint64_t m = st->mpiv[j];  // only steps before j
+      uint64_t acc = 0;
+      if ((m >> lane) & 1u) acc ^= sE[lane];
+      if ((m >> (lane + 32)) & 1u) acc ^= sE[lane + 32];
+      for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) sE[j] = acc ^ (1ull << j);
+      __syncwarp();
     }
   }
   __syncthreads();
-  if (threadIdx.x < (uint32_t)L) {
-    const int j = threadIdx.x;
-    if (sA[j]) atomicAdd(&st->A[j], sA[j]);
-    if (sB[j]) atomicAdd(&st->B0[j], sB[j]);
-    if (sC[j]) atomicXor(&st->Cp[j], sC[j]);
-    if (sG[j]) atomicXor(reinterpret_cast<unsigned long long *>(&st->G[j]), sG[j]);
+  for (int j = w; j < L; j += nw) {
+    const uint64_t x0 = ox[j][lane], z0 = oz[j][lane];
+    uint64_t ax = x0, az = z0, e = sE[j] & ~(1ull << j);
+    while (e) {
+      const int s = __ffsll((long long)e) - 1;
+      e &= e - 1;
+      ax ^= ox[s][lane];
+      az ^= oz[s][lane];
+    }
+    vx[j][lane] = ax;
+    vz[j][lane] = az;
+    if (in) {
+      VX[(uint64_t)j * rs + u] = ax;
+      VZ[(uint64_t)j * rs + u] = az;
+    }
+    int a = __popcll(ax & az), b = __popcll(x0 & z0);
+    const uint32_t c = __ballot_sync(0xffffffffu, __popcll((az ^ z0) & x0) & 1);
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      if (a) atomicAdd(&st->A[j], a);
+      if (b) atomicAdd(&st->B0[j], b);
+      if (__popc(c) & 1) atomicXor(&st->Cp[j], 1);
+    }
+  }
+  __syncthreads();
+  // G[s] bit t = parity of z_{V_s} . x_{V_t} over the chunk
+  for (int s = w; s < L; s += nw) {
+    const uint64_t zs = vz[s][lane];
+    uint64_t row = 0;
+    for (int t = 0; t < L; ++t) {
+      const uint32_t bal = __ballot_sync(0xffffffffu, __popcll(zs & vx[t][lane]) & 1);
+      row |= (uint64_t)(__popc(bal) & 1) << t;
+    }
+    if (lane == 0 && row) atomicXor(reinterpret_cast<unsigned long long *>(&st->G[s]), row);
   }
 }
 
@@ -209,11 +242,16 @@ __device__ __forceinline__ int cross_pairs(const uint64_t *G, uint64_t m) {
   return par;
 }
 
-// signs of V_j in step order (one thread)
-__global__ void blk_signs_kernel(const uint64_t *__restrict__ S, BlkState *st, uint32_t *err) {
-  if (threadIdx.x != 0) return;
-  const int L = st->len;
-  for (int j = 0; j < L; ++j) {
+// signs of V_j. The phase exponent of step j is
+//   e_j = 2 r(p_j) + B0_j - A_j + 2 Cp_j + sum_{s in m_j} (2 rV_s + A_s) + 2 cross(m_j)
+// (mod 4); everything but the 2 rV_s terms is independent of the other steps and
+// is computed by one thread per step, then one thread resolves the signs in
+// step order: rV_j = (e'_j >> 1) ^ parity(m_j & {s : rV_s = 1}).
+__global__ void __launch_bounds__(64) blk_signs_kernel(const uint64_t *__restrict__ S, BlkState *st,
+                                                       uint32_t *err) {
+  __shared__ int sb[64];
+  const int L = st->len, j = threadIdx.x;
+  if (j < L) {
     const int64_t p = st->piv[j];
     const uint64_t m = st->mpiv[j];
     int e = 2 * (int)((S[p >> 6] >> (p & 63)) & 1u) + st->B0[j] - st->A[j] + 2 * st->Cp[j];
@@ -221,83 +259,203 @@ __global__ void blk_signs_kernel(const uint64_t *__restrict__ S, BlkState *st, u
     while (mm) {
       const int s = __ffsll((long long)mm) - 1;
       mm &= mm - 1;
-      e += 2 * st->rV[s] + st->A[s];
+      e += st->A[s];
     }
     e += 2 * cross_pairs(st->G, m);
-    e = m4(e);
-    if (e & 1) atomicOr(err, kErrOddPhase);
-    st->rV[j] = e >> 1;
+    sb[j] = m4(e);
+  }
+  __syncthreads();
+  if (j == 0) {
+    uint64_t R = 0;
+    for (int i = 0; i < L; ++i) {
+      const int e = sb[i];
+      if (e & 1) atomicOr(err, kErrOddPhase);
+      const int rv = (e >> 1) ^ (__popcll(st->mpiv[i] & R) & 1);
+      st->rV[i] = rv;
+      R |= (uint64_t)rv << i;
+    }
   }
 }
 
-// phase 3: block = one chunk of kCW column words x a range of rows; warp per row
-__global__ void __launch_bounds__(256)
-blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t rs, uint64_t nrows,
+// phase 3: block = one chunk of kCW (32) column words x a range of rows.
+// The XOR of any subset of the 64 V rows is assembled from tables of XOR
+// combinations of consecutive steps (the "Four Russians" method): steps are cut
+// into 12 groups of 5 and one of 4, and T[g][c] = XOR of V[5g + b] over the bits
+// b of c, built once per block in shared memory (200 KB), so a row needs 13
+// lookups. A warp handles one row (lane = column word, x and z side by side in
+// one 16-byte table entry, 512 bytes per entry); a row segment is 256 contiguous
+// bytes of each matrix, the shortest that keeps HBM fully efficient. Each warp
+// keeps the next two rows' loads in flight while it works on the current one;
+// the row loop is unrolled by three so the in-flight rows rotate through
+// registers without copies.
+constexpr int kGroups = 13, kGroupBits = 5;
+constexpr int kEntries = 12 * 32 + 16;  // 400 table entries of kCW (x, z) word pairs
+constexpr int kEntryBytes = kCW * 16;   // 512
+__host__ __device__ constexpr int group_base(int g) { return 32 * g; }
+__host__ __device__ constexpr int group_size(int g) { return g < 12 ? 32 : 16; }
+
+struct ApplyRow {
+  int32_t b;
+  uint32_t lo, hi;  // M_r
+  uint2 x, z;       // this lane's word of x and z, as 32-bit halves
+};
+
+// Idx: 32-bit offsets when the row-major matrix has fewer than 2^32 words
+template <typename Idx>
+__device__ __forceinline__ void apply_fetch(ApplyRow &a, uint32_t r, uint32_t nrows, const uint64_t *RX,
+                                            const uint64_t *RZ, Idx off, bool ok, const uint64_t *M,
+                                            const int32_t *base) {
+  a.b = kBaseOrig;
+  a.lo = a.hi = 0;
+  a.x = a.z = make_uint2(0, 0);
+  if (r < nrows) {
+    a.b = __ldg(base + r);
+    const uint2 m = __ldg(reinterpret_cast<const uint2 *>(M) + r);
+    a.lo = m.x;
+    a.hi = m.y;
+    if (ok) {
+      a.x = reinterpret_cast<const uint2 *>(RX)[off];
+      a.z = reinterpret_cast<const uint2 *>(RZ)[off];
+    }
+  }
+}
+
+// a ^ b ^ c in one three-input logic operation
+__device__ __forceinline__ uint32_t xor3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ void acc3(uint4 &a, const uint4 &p, const uint4 &q) {
+  a.x = xor3(a.x, p.x, q.x);
+  a.y = xor3(a.y, p.y, q.y);
+  a.z = xor3(a.z, p.z, q.z);
+  a.w = xor3(a.w, p.w, q.w);
+}
+
+// byte offset (pattern * 512) of the entry of group g, from the 32-bit halves of M_r
+template <int g>
+__device__ __forceinline__ uint32_t pat_off(uint32_t lo, uint32_t hi) {
+  constexpr int sh = kGroupBits * g;
+  constexpr uint32_t mask = (uint32_t)(group_size(g) - 1) * kEntryBytes;
+  if constexpr (sh + kGroupBits <= 32) {
+    if constexpr (sh >= 9) return (lo >> (sh - 9)) & mask;
+    else return (lo << (9 - sh)) & mask;
+  } else if constexpr (sh >= 32) {
+    if constexpr (sh - 32 >= 9) return (hi >> (sh - 32 - 9)) & mask;
+    else return (hi << (9 - (sh - 32))) & mask;
+  } else {
+    return __funnelshift_r(lo, hi, sh - 9) & mask;  // bits straddle the halves
+  }
+}
+
+// table entry of group g for this lane: (x lo, x hi, z lo, z hi)
+template <int g>
+__device__ __forceinline__ uint4 tab(const char *tl, uint32_t lo, uint32_t hi) {
+  return *reinterpret_cast<const uint4 *>(tl + group_base(g) * kEntryBytes + pat_off<g>(lo, hi));
+}
+
+template <typename Idx>
+__device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t r, uint32_t nrows, uint64_t *RX,
+                                          uint64_t *RZ, Idx off, bool ok, uint32_t word,
+                                          const uint32_t *qubits, const uint64_t *VX,
+                                          const uint64_t *VZ, uint32_t rs, uint32_t lane,
+                                          const char *tl, int32_t *Tp, uint64_t tp0) {
+  if (r >= nrows) return;  // uniform over the warp
+  uint2 *px = reinterpret_cast<uint2 *>(RX), *pz = reinterpret_cast<uint2 *>(RZ);
+  if (a.b >= kBasePivot) {  // pivot row of step j: +-Z_q (sign set by blk_rows_kernel)
+    const uint32_t q = qubits[a.b - kBasePivot];
+    if (ok) {
+      px[off] = make_uint2(0, 0);
+      const uint32_t bit = ((q >> 6) == word) ? 1u << (q & 31) : 0u;
+      pz[off] = (q & 32) ? make_uint2(0, bit) : make_uint2(bit, 0);
+    }
+    return;
+  }
+  if (a.b == kBaseOrig && (a.lo | a.hi) == 0) return;
+  uint2 xb = a.x, zb = a.z;
+  if (a.b != kBaseOrig && ok) {  // destabilizer replaced by V_b at step b
+    xb = reinterpret_cast<const uint2 *>(VX)[(uint64_t)a.b * rs + word];
+    zb = reinterpret_cast<const uint2 *>(VZ)[(uint64_t)a.b * rs + word];
+  }
+  // branch-free: pattern 0 is a zero entry, so all 13 loads can be in flight together
+  const uint32_t lo = a.lo, hi = a.hi;
+  uint4 acc = tab<0>(tl, lo, hi);
+  acc3(acc, tab<1>(tl, lo, hi), tab<2>(tl, lo, hi));
+  acc3(acc, tab<3>(tl, lo, hi), tab<4>(tl, lo, hi));
+  acc3(acc, tab<5>(tl, lo, hi), tab<6>(tl, lo, hi));
+  acc3(acc, tab<7>(tl, lo, hi), tab<8>(tl, lo, hi));
+  acc3(acc, tab<9>(tl, lo, hi), tab<10>(tl, lo, hi));
+  acc3(acc, tab<11>(tl, lo, hi), tab<12>(tl, lo, hi));
+  const uint2 xf = make_uint2(xb.x ^ acc.x, xb.y ^ acc.y), zf = make_uint2(zb.x ^ acc.z, zb.y ^ acc.w);
+  if (ok) {
+    px[off] = xf;
+    pz[off] = zf;
+  }
+  // t = |x_b & z_b| - |x_f & z_f| summed over the chunk, c = parity of z_acc . x_b;
+  // one warp reduction of 64 t + c (0 <= sum of c <= 32)
+  const int t = __popc(xb.x & zb.x) + __popc(xb.y & zb.y) - __popc(xf.x & zf.x) - __popc(xf.y & zf.y);
+  const int c = (__popc(acc.z & xb.x) + __popc(acc.w & xb.y)) & 1;
+  const int v = __reduce_add_sync(0xffffffffu, 64 * t + c);
+  if (lane == 0) Tp[tp0 + r] = (v >> 6) * 2 + (v & 1);
+}
+
+template <typename Idx>
+__global__ void __launch_bounds__(1024)
+blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t rs, uint32_t nrows,
                  const uint32_t *__restrict__ qubits, const uint64_t *__restrict__ VX,
                  const uint64_t *__restrict__ VZ, const uint64_t *__restrict__ M,
                  const int32_t *__restrict__ base, int32_t *__restrict__ Tp, const BlkState *st) {
-  extern __shared__ ulonglong2 sv[];  // [64][kCW/2] x words, then [64][kCW/2] z words
-  ulonglong2(*svx)[kCW / 2] = reinterpret_cast<ulonglong2(*)[kCW / 2]>(sv);
-  ulonglong2(*svz)[kCW / 2] = reinterpret_cast<ulonglong2(*)[kCW / 2]>(sv + 64 * (kCW / 2));
+  extern __shared__ ulonglong2 T[];  // [kEntries][kCW] of (x word, z word)
   const int L = st->len;
   const uint32_t u0 = blockIdx.x * kCW;  // first column word of the chunk
-  const uint32_t nv = min((uint32_t)kCW, rs - u0) / 2;
-  for (int i = threadIdx.x; i < L * (kCW / 2); i += blockDim.x) {
-    const int s = i / (kCW / 2), v = i % (kCW / 2);
-    if ((uint32_t)v < nv) {
-      svx[s][v] = *reinterpret_cast<const ulonglong2 *>(VX + (uint64_t)s * rs + u0 + 2 * v);
-      svz[s][v] = *reinterpret_cast<const ulonglong2 *>(VZ + (uint64_t)s * rs + u0 + 2 * v);
+  const uint32_t nw = min((uint32_t)kCW, rs - u0);
+  // table: entry 0 of a group is zero; entry c = entry (c with its lowest bit
+  // cleared) ^ V[5g + lowest bit of c]
+  for (int i = threadIdx.x; i < kGroups * kCW; i += blockDim.x) {
+    const int g = i / kCW, w = i % kCW;
+    ulonglong2 vv[kGroupBits];
+#pragma unroll
+    for (int b = 0; b < kGroupBits; ++b) {
+      const int s = kGroupBits * g + b;
+      vv[b] = make_ulonglong2(0, 0);
+      if (s < L && s < 64 && (uint32_t)w < nw)
+        vv[b] = make_ulonglong2(VX[(uint64_t)s * rs + u0 + w], VZ[(uint64_t)s * rs + u0 + w]);
+    }
+    const int e0 = group_base(g), ne = group_size(g);
+    T[e0 * kCW + w] = make_ulonglong2(0, 0);
+#pragma unroll
+    for (int c = 1; c < 32; ++c) {
+      if (c >= ne) break;
+      const int lb = (c & 1) ? 0 : (c & 2) ? 1 : (c & 4) ? 2 : (c & 8) ? 3 : 4, prev = c & (c - 1);
+      const ulonglong2 pv = T[(e0 + prev) * kCW + w];
+      T[(e0 + c) * kCW + w] = make_ulonglong2(pv.x ^ vv[lb].x, pv.y ^ vv[lb].y);
     }
   }
   __syncthreads();
   if (L == 0) return;
-  const int lane = threadIdx.x & 31;
-  const uint64_t warps = (uint64_t)gridDim.y * (blockDim.x >> 5);
-  const uint64_t w0 = (uint64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  for (uint64_t r = w0; r < nrows; r += warps) {
-    const int32_t b = base[r];
-    const uint64_t sr = M[r];
-    if (b == kBaseOrig && sr == 0) continue;
-    ulonglong2 *rx = reinterpret_cast<ulonglong2 *>(RX + r * rs + u0);
-    ulonglong2 *rz = reinterpret_cast<ulonglong2 *>(RZ + r * rs + u0);
-    if (b >= kBasePivot) {  // pivot row of step j: +-Z_q (sign set by blk_rows_kernel)
-      const uint32_t q = qubits[b - kBasePivot];
-      for (uint32_t v = lane; v < nv; v += 32) {
-        rx[v] = make_ulonglong2(0, 0);
-        const uint32_t w = u0 + 2 * v;
-        ulonglong2 zz = make_ulonglong2(0, 0);
-        if ((q >> 6) == w) zz.x = 1ull << (q & 63);
-        if ((q >> 6) == w + 1) zz.y = 1ull << (q & 63);
-        rz[v] = zz;
-      }
-      continue;
-    }
-    int t = 0, c = 0;
-    for (uint32_t v = lane; v < nv; v += 32) {
-      ulonglong2 xb, zb;
-      if (b == kBaseOrig) { xb = rx[v]; zb = rz[v]; }
-      else { xb = svx[b][v]; zb = svz[b][v]; }
-      ulonglong2 xa = make_ulonglong2(0, 0), za = make_ulonglong2(0, 0);
-      uint64_t m = sr;
-      while (m) {
-        const int s = __ffsll((long long)m) - 1;
-        m &= m - 1;
-        const ulonglong2 a = svx[s][v], bz = svz[s][v];
-        xa.x ^= a.x; xa.y ^= a.y;
-        za.x ^= bz.x; za.y ^= bz.y;
-      }
-      const ulonglong2 xf = make_ulonglong2(xb.x ^ xa.x, xb.y ^ xa.y);
-      const ulonglong2 zf = make_ulonglong2(zb.x ^ za.x, zb.y ^ za.y);
-      t += __popcll(xb.x & zb.x) + __popcll(xb.y & zb.y) - __popcll(xf.x & zf.x) - __popcll(xf.y & zf.y);
-      c ^= (__popcll(za.x & xb.x) + __popcll(za.y & xb.y)) & 1;
-      rx[v] = xf;
-      rz[v] = zf;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      t += __shfl_xor_sync(0xffffffffu, t, o);
-      c ^= __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    if (lane == 0) Tp[(uint64_t)blockIdx.x * nrows + r] = t * 2 + (c & 1);
+  const uint32_t lane = threadIdx.x & 31;
+  const bool ok = lane < nw;
+  const uint32_t word = u0 + lane;
+  const char *tl = reinterpret_cast<const char *>(T) + lane * 16;
+  const uint32_t units = gridDim.y * (blockDim.x >> 5);
+  const Idx step = (Idx)units * rs;
+  const uint64_t tp0 = (uint64_t)blockIdx.x * nrows;
+  uint32_t r = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  Idx off = (Idx)r * rs + word;
+  // unrolled by three so the rows in flight rotate through registers without copies
+  ApplyRow a0, a1, a2;
+  apply_fetch<Idx>(a0, r, nrows, RX, RZ, off, ok, M, base);
+  apply_fetch<Idx>(a1, r + units, nrows, RX, RZ, off + step, ok, M, base);
+  for (; r < nrows; r += 3 * units, off += 3 * step) {
+    apply_fetch<Idx>(a2, r + 2 * units, nrows, RX, RZ, off + 2 * step, ok, M, base);
+    apply_row<Idx>(a0, r, nrows, RX, RZ, off, ok, word, qubits, VX, VZ, rs, lane, tl, Tp, tp0);
+    apply_fetch<Idx>(a0, r + 3 * units, nrows, RX, RZ, off + 3 * step, ok, M, base);
+    apply_row<Idx>(a1, r + units, nrows, RX, RZ, off + step, ok, word, qubits, VX, VZ, rs, lane, tl, Tp,
+                   tp0);
+    apply_fetch<Idx>(a1, r + 4 * units, nrows, RX, RZ, off + 4 * step, ok, M, base);
+    apply_row<Idx>(a2, r + 2 * units, nrows, RX, RZ, off + 2 * step, ok, word, qubits, VX, VZ, rs, lane,
+                   tl, Tp, tp0);
   }
 }
 
@@ -385,20 +543,32 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   for (int j = 0; j < B; ++j)
     blk_step_kernel<<<rb, 256, 0, s>>>(L.nrows, L.n, L.k, j, B, (j & 1) ? C1 : C0,
                                        (j & 1) ? C0 : C1, M, base, st);
-  blk_vrows_kernel<<<(L.rs + 127) / 128, 128, 0, s>>>(d.RX, d.RZ, L.rs, L.k, VX, VZ, st);
-  blk_signs_kernel<<<1, 32, 0, s>>>(d.S, st, d.err);
-  const size_t smem = 2ull * 64 * (kCW / 2) * sizeof(ulonglong2);
+  const size_t smem = (size_t)kEntries * kEntryBytes;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !((g_apply_attr_set >> dev) & 1u)) {
-    cudaError_t e = cudaFuncSetAttribute(blk_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(blk_apply_kernel<uint32_t>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(blk_apply_kernel<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(blk_vrows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kVrowSmem);
     if (e != cudaSuccess) return e;
     g_apply_attr_set |= 1ull << dev;
   }
-  const uint32_t rows_y = std::max<uint32_t>(1, (uint32_t)std::min<uint64_t>((uint64_t)d.sms * 8 / chunks + 1, L.nrows / 8 + 1));
-  blk_apply_kernel<<<dim3(chunks, rows_y), 256, smem, s>>>(d.RX, d.RZ, L.rs, L.nrows, qubits, VX,
-                                                           VZ, M, base, Tp, st);
+  blk_vrows_kernel<<<chunks, kVrowThreads, kVrowSmem, s>>>(d.RX, d.RZ, L.rs, VX, VZ, st);
+  blk_signs_kernel<<<1, 64, 0, s>>>(d.S, st, d.err);
+  // about 8 waves of one block per SM (the table takes 200 KB of shared memory)
+  const uint32_t rows_y = std::max<uint32_t>(
+      1, (uint32_t)std::min<uint64_t>(((uint64_t)d.sms * 8 + chunks - 1) / chunks, L.nrows / 64 + 1));
+  if ((uint64_t)L.nrows * L.rs < (1ull << 32))
+    blk_apply_kernel<uint32_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
+        d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, M, base, Tp, st);
+  else
+    blk_apply_kernel<uint64_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
+        d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, M, base, Tp, st);
   blk_rows_kernel<<<rb, 256, 0, s>>>(d.S, L.nrows, qubits, M, base, Tp, chunks, st, m0, key.seed,
                                      key.shot, d.record, d.err);
   if (launches) *launches += 6 + B;
