@@ -28,6 +28,13 @@
  *     sigma(x_hj,z_hj).
  *   - Pauli-frame sampling of Sec. 5 (Alg. 9) with a reference record
  *     (the frames carry flips relative to that record).
+ *   - Pauli noise channels on the frames (Sec. 3 notes that frames carry
+ *     error events as well as measurement randomness; the paper fixes no
+ *     channel set or sampling rule, so these are a reading): X_ERROR(p),
+ *     Y_ERROR(p), Z_ERROR(p) apply their Pauli with probability p;
+ *     DEPOLARIZE1(p) applies one of X, Y, Z, each with probability p/3;
+ *     DEPOLARIZE2(p) applies one of the 15 non-identity two-qubit Paulis,
+ *     each with probability p/15. The tableau (reference shot) is noiseless.
  *
  * Readings of the paper where it is silent or garbled (listed in the design
  * notes): the rowsum goes into every row i != p (both halves) with x_iq = 1,
@@ -41,6 +48,13 @@
  *                                                     key=(seed, 0x51A7E))
  *   frame_word(seed, e, q, j) = word (j & 3) of Philox(ctr=(e, q, j >> 2, 1),
  *                                                     key=(seed, 0xF4A3E))
+ *   noise_draw(seed, e, i, s) = words (2h, 2h + 1) = (u, v) of
+ *       Philox(ctr=(e, i, 32 (s >> 6) + (s & 31), 3), key=(seed, 0xE5505)),
+ *       h = (s >> 5) & 1, for target i of noise op e (ops numbered from 0 in
+ *       program order) and shot s. The channel fires iff p >= 1 or
+ *       u < floor(p * 2^64); the Pauli is picked by floor(v * 3 / 2^64)
+ *       (X, Y, Z) or floor(v * 15 / 2^64) + 1 (two-qubit Pauli index
+ *       4 a + b with 0 = I, 1 = X, 2 = Y, 3 = Z).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -84,6 +98,28 @@ uint64_t oracle_frame_word(uint64_t seed, uint64_t e, uint64_t q, uint64_t j) {
   uint64_t ctr[4] = {e, q, j >> 2, 1}, key[2] = {seed, 0xF4A3Eull}, out[4];
   oracle_philox4x64_10(ctr, key, out);
   return out[j & 3];
+}
+
+void oracle_noise_draw(uint64_t seed, uint64_t e, uint64_t i, uint64_t s, uint64_t *u, uint64_t *v) {
+  uint64_t j = s >> 6, b = s & 63u, half = b >> 5;
+  uint64_t ctr[4] = {e, i, 32u * j + (b & 31u), 3}, key[2] = {seed, 0xE5505ull}, out[4];
+  oracle_philox4x64_10(ctr, key, out);
+  *u = out[2 * half];
+  *v = out[2 * half + 1];
+}
+
+/* floor(p * 2^64) for 0 <= p < 1 (multiplying by a power of two is exact) */
+uint64_t oracle_noise_threshold(double p) {
+  if (!(p > 0.0)) return 0;
+  if (p >= 1.0) return UINT64_MAX;
+  return (uint64_t)(p * 18446744073709551616.0);
+}
+
+/* floor(v * k / 2^64): the high word of the 128-bit product */
+static uint64_t mul_hi(uint64_t v, uint64_t k) {
+  uint64_t hi, lo;
+  mul128(v, k, &hi, &lo);
+  return hi;
 }
 
 /* ------------------------------------------------------------------ */
@@ -348,18 +384,54 @@ static void frame_gate(uint8_t *fx, uint8_t *fz, int type, int a, int b) {
   }
 }
 
+enum { N_X, N_Y, N_Z, N_DEP1, N_DEP2 };
+
+/* Pauli code 0 = I, 1 = X, 2 = Y, 3 = Z on the frame of qubit q */
+static void frame_pauli(uint8_t *fx, uint8_t *fz, int q, int code) {
+  if (code == 1 || code == 2) fx[q] ^= 1u;
+  if (code == 2 || code == 3) fz[q] ^= 1u;
+}
+
+/* noise op e with targets t[0..cnt) (pairs for DEPOLARIZE2), shot s */
+static void frame_noise(uint8_t *fx, uint8_t *fz, int kind, double p, const uint32_t *t, long cnt,
+                        uint64_t e, uint64_t seed, uint64_t s) {
+  const uint64_t thr = oracle_noise_threshold(p);
+  const long targets = kind == N_DEP2 ? cnt / 2 : cnt;
+  for (long i = 0; i < targets; ++i) {
+    uint64_t u, v;
+    oracle_noise_draw(seed, e, (uint64_t)i, s, &u, &v);
+    int fire = p >= 1.0 || u < thr;
+    if (!fire) continue;
+    switch (kind) {
+      case N_X: frame_pauli(fx, fz, (int)t[i], 1); break;
+      case N_Y: frame_pauli(fx, fz, (int)t[i], 2); break;
+      case N_Z: frame_pauli(fx, fz, (int)t[i], 3); break;
+      case N_DEP1: frame_pauli(fx, fz, (int)t[i], 1 + (int)mul_hi(v, 3)); break;
+      case N_DEP2: {
+        int idx = 1 + (int)mul_hi(v, 15);
+        frame_pauli(fx, fz, (int)t[2 * i], idx >> 2);
+        frame_pauli(fx, fz, (int)t[2 * i + 1], idx & 3);
+        break;
+      }
+      default: break;
+    }
+  }
+}
+
 /*
  * Samples `shots` shots of a program given as a list of ops:
  *   op_kind[o] = 0: apply gates[op_a[o] .. op_b[o]) (rows of 3 uint32)
  *   op_kind[o] = 1: measure qubits[op_a[o] .. op_b[o]) in order
+ *   op_kind[o] = 2: noise channel noise_kind[o] with probability noise_p[o]
+ *                   on the targets qubits[op_a[o] .. op_b[o])
  * ref[m] is the reference outcome of measurement m (program order).
  * out[m * shots + s] = outcome bit of measurement m in shot s.
  * Frame init: fx = 0, fz[q] = bit (s mod 64) of frame_word(seed, 0, q, s/64);
  * after measurement m of q: fz[q] = bit of frame_word(seed, m + 1, q, s/64).
  */
 int oracle_frames(int n, const uint32_t *gates, const uint32_t *qubits, const int *op_kind,
-                  const long *op_a, const long *op_b, long n_ops, const uint8_t *ref,
-                  long shots, uint64_t seed, uint8_t *out) {
+                  const long *op_a, const long *op_b, const int *noise_kind, const double *noise_p,
+                  long n_ops, const uint8_t *ref, long shots, uint64_t seed, uint8_t *out) {
   uint8_t *fx = (uint8_t *)calloc((size_t)n, 1), *fz = (uint8_t *)calloc((size_t)n, 1);
   if (!fx || !fz) { free(fx); free(fz); return -1; }
   for (long s = 0; s < shots; ++s) {
@@ -369,10 +441,14 @@ int oracle_frames(int n, const uint32_t *gates, const uint32_t *qubits, const in
       fz[q] = (uint8_t)((oracle_frame_word(seed, 0, (uint64_t)q, j) >> bit) & 1u);
     }
     long m = 0;
+    uint64_t e = 0; /* noise ops so far */
     for (long o = 0; o < n_ops; ++o) {
       if (op_kind[o] == 0) {
         for (long g = op_a[o]; g < op_b[o]; ++g)
           frame_gate(fx, fz, (int)gates[3 * g], (int)gates[3 * g + 1], (int)gates[3 * g + 2]);
+      } else if (op_kind[o] == 2) {
+        frame_noise(fx, fz, noise_kind[o], noise_p[o], qubits + op_a[o], op_b[o] - op_a[o], e++, seed,
+                    (uint64_t)s);
       } else {
         for (long i = op_a[o]; i < op_b[o]; ++i, ++m) {
           int q = (int)qubits[i];

@@ -75,7 +75,12 @@ def load_library(path: str):
     L.oracle_frames.restype = ctypes.c_int
     L.oracle_frames.argtypes = [ctypes.c_int, _u32p, _u32p, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                 ctypes.c_long, _u8p, ctypes.c_long, ctypes.c_uint64, _u8p]
+    L.oracle_noise_draw.restype = None
+    L.oracle_noise_draw.argtypes = [ctypes.c_uint64] * 4 + [_u64p, _u64p]
+    L.oracle_noise_threshold.restype = ctypes.c_uint64
+    L.oracle_noise_threshold.argtypes = [ctypes.c_double]
     return L
 
 
@@ -211,14 +216,15 @@ class RowSubset:
 
 def run_circuit(circuit, seed: int, shot: int = 0, force_zero: bool = False,
                 oracle: Optional[Oracle] = None):
-    """Runs a workloads.circuits.Circuit single-shot. Returns (oracle, record,
-    kinds) with the record in program order."""
+    """Runs a workloads.circuits.Circuit single-shot (the noiseless reference
+    shot: noise ops act on the frames only). Returns (oracle, record, kinds)
+    with the record in program order."""
     o = oracle or Oracle(circuit.n)
     rec, kinds = [], []
     for op in circuit.ops:
         if op[0] == "layers":
             o.apply(circuit.gates[circuit.layer_ptr[op[1]]:circuit.layer_ptr[op[2]]])
-        else:
+        elif op[0] == "measure":
             out, kind = o.measure(op[1], seed, shot, force_zero)
             rec.append(out)
             kinds.append(kind)
@@ -227,23 +233,43 @@ def run_circuit(circuit, seed: int, shot: int = 0, force_zero: bool = False,
     return o, rec, kinds
 
 
+def noise_draw(seed: int, e: int, i: int, s: int):
+    """(u, v) random words of target i of noise op e in shot s."""
+    u, v = ctypes.c_uint64(), ctypes.c_uint64()
+    lib().oracle_noise_draw(seed, e, i, s, ctypes.byref(u), ctypes.byref(v))
+    return u.value, v.value
+
+
+def noise_threshold(p: float) -> int:
+    """floor(p * 2^64) for 0 <= p < 1 (0 for p <= 0, 2^64 - 1 for p >= 1)."""
+    return int(lib().oracle_noise_threshold(p))
+
+
 def frames(circuit, ref: np.ndarray, shots: int, seed: int) -> np.ndarray:
-    """Pauli-frame samples of `circuit` (Sec. 5). Returns (M, shots) uint8."""
-    kinds, a, b, qlist = [], [], [], []
+    """Pauli-frame samples of `circuit` (Sec. 5), with its noise ops applied to
+    the frames. Returns (M, shots) uint8."""
+    kinds, a, b, qlist, nk, npr = [], [], [], [], [], []
     qoff = 0
+    M = 0
     for op in circuit.ops:
         if op[0] == "layers":
             kinds.append(0)
             a.append(int(circuit.layer_ptr[op[1]]))
             b.append(int(circuit.layer_ptr[op[2]]))
-        else:
-            kinds.append(1)
-            a.append(qoff)
-            qoff += len(op[1])
-            b.append(qoff)
-            qlist.append(np.asarray(op[1], np.uint32))
+            nk.append(0)
+            npr.append(0.0)
+            continue
+        targets = np.asarray(op[1] if op[0] == "measure" else op[3], np.uint32)
+        kinds.append(1 if op[0] == "measure" else 2)
+        nk.append(0 if op[0] == "measure" else int(op[1]))
+        npr.append(0.0 if op[0] == "measure" else float(op[2]))
+        a.append(qoff)
+        qoff += len(targets)
+        b.append(qoff)
+        qlist.append(targets)
+        if op[0] == "measure":
+            M += len(targets)
     q = np.concatenate(qlist) if qlist else np.zeros(1, np.uint32)
-    M = qoff
     ref = np.ascontiguousarray(ref, np.uint8)
     assert len(ref) == M
     g = np.ascontiguousarray(circuit.gates, np.uint32)
@@ -253,10 +279,14 @@ def frames(circuit, ref: np.ndarray, shots: int, seed: int) -> np.ndarray:
     ka = np.array(kinds, np.intc)
     aa = np.array(a, np.int_)
     ba = np.array(b, np.int_)
+    nka = np.array(nk, np.intc)
+    npa = np.array(npr, np.float64)
     rc = lib().oracle_frames(circuit.n, _p(g, _u32p), _p(q, _u32p),
                              ka.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                              aa.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
-                             ba.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), len(kinds),
+                             ba.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                             nka.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                             npa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(kinds),
                              _p(ref if M else np.zeros(1, np.uint8), _u8p), shots, seed,
                              _p(out, _u8p))
     if rc != 0:

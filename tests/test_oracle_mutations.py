@@ -18,6 +18,7 @@ from oracle import oracle as O
 from tests import test_oracle_frames as TF
 from tests import test_oracle_gates as TG
 from tests import test_oracle_measure as TM
+from tests import test_oracle_noise as TN
 from workloads import circuits as C
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
@@ -50,6 +51,15 @@ def _pins_frames():
     TF.test_frames_support_and_distribution(5, 2, 3, 0.4)
     TF.test_frames_support_and_distribution(6, 3, 4, 0.5)
     TF.test_frames_reference_is_deterministic_part()
+
+
+def _pins_noise():
+    for seed in (1, 2, 3):
+        TN.test_noisy_frames_match_exact_distribution(seed)
+    for kind, flip in [(C.NOISE_X, 1), (C.NOISE_Y, 1), (C.NOISE_Z, 0)]:
+        TN.test_certain_errors_on_z_eigenstate(kind, flip)
+    TN.test_certain_errors_propagate_through_h_and_cx()
+    TN.test_flip_rates()
 
 
 MUTATIONS = [
@@ -89,6 +99,19 @@ MUTATIONS = [
      ";", _pins_frames),
     ("frames drop the reference record",
      "(uint8_t)(fx[q] ^ ref[m]);", "(uint8_t)(fx[q]);", _pins_frames),
+    ("noise fires above the threshold",
+     "int fire = p >= 1.0 || u < thr;", "int fire = p >= 1.0 || u > thr;", _pins_noise),
+    ("Y error flips only z",
+     "if (code == 1 || code == 2) fx[q] ^= 1u;", "if (code == 1) fx[q] ^= 1u;", _pins_noise),
+    ("DEPOLARIZE1 can pick the identity",
+     "case N_DEP1: frame_pauli(fx, fz, (int)t[i], 1 + (int)mul_hi(v, 3)); break;",
+     "case N_DEP1: frame_pauli(fx, fz, (int)t[i], (int)mul_hi(v, 4)); break;", _pins_noise),
+    ("DEPOLARIZE2 applies the same Pauli to both qubits",
+     "frame_pauli(fx, fz, (int)t[2 * i + 1], idx & 3);",
+     "frame_pauli(fx, fz, (int)t[2 * i + 1], idx >> 2);", _pins_noise),
+    ("noise ops share one random stream",
+     "noise_p[o], qubits + op_a[o], op_b[o] - op_a[o], e++, seed,",
+     "noise_p[o], qubits + op_a[o], op_b[o] - op_a[o], 0, seed,", _pins_noise),
 ]
 
 
@@ -116,3 +139,4 @@ def test_unmutated_oracle_passes_the_same_pins():
     _pins_measure()
     _pins_philox()
     _pins_frames()
+    _pins_noise()

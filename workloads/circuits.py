@@ -32,6 +32,10 @@ I, X, Y, Z, H, S, SDG, CX, CY, CZ, SWAP, ISWAP = range(12)
 GATE_NAMES = ["I", "X", "Y", "Z", "H", "S", "SDG", "CX", "CY", "CZ", "SWAP", "ISWAP"]
 TWO_QUBIT = (CX, CY, CZ, SWAP, ISWAP)
 
+# Pauli noise channel codes (frames only; the C header declares the same values)
+NOISE_X, NOISE_Y, NOISE_Z, DEPOLARIZE1, DEPOLARIZE2 = range(5)
+NOISE_NAMES = ["X_ERROR", "Y_ERROR", "Z_ERROR", "DEPOLARIZE1", "DEPOLARIZE2"]
+
 _SINGLE_DRAW = np.array([H, S, I], dtype=np.uint32)
 
 
@@ -41,8 +45,10 @@ class Circuit:
 
     gates:     (G, 3) uint32 rows (type, q0, q1); q1 is 0 for one-qubit gates.
     layer_ptr: (L+1,) int64; layer l is gates[layer_ptr[l]:layer_ptr[l+1]].
-    ops:       program order, a list of ("layers", l0, l1) and
-               ("measure", qubits uint32 array) entries.
+    ops:       program order, a list of ("layers", l0, l1),
+               ("measure", qubits uint32 array) and
+               ("noise", kind, p, targets uint32 array) entries; noise acts
+               on the sampled shots only (pairs of targets for DEPOLARIZE2).
     """
 
     n: int
@@ -234,3 +240,31 @@ def serving_requests(count: int, rate_hz: float, seed: int = 5) -> List[Request]
     f = np.round(np.exp(rng.uniform(np.log(1e3), np.log(1e6), size=count))).astype(int)
     return [Request(float(t[i]), int(n[i]), int(d[i]), int(f[i]), seed * 1_000_003 + i)
             for i in range(count)]
+
+
+def with_circuit_noise(circ: Circuit, p_gate: float, p_meas: float) -> Circuit:
+    """The same circuit with circuit-level Pauli noise on its sampled shots:
+    after every layer, DEPOLARIZE1(p_gate) on the qubits of its one-qubit
+    gates and DEPOLARIZE2(p_gate) on the pairs of its two-qubit gates; before
+    every measurement window, X_ERROR(p_meas) on the measured qubits."""
+    ops: List[Tuple] = []
+    for op in circ.ops:
+        if op[0] == "layers":
+            for l in range(op[1], op[2]):
+                ops.append(("layers", l, l + 1))
+                g = circ.layer(l)
+                two = np.isin(g[:, 0], TWO_QUBIT)
+                one = ~two & (g[:, 0] != I)
+                if p_gate > 0 and one.any():
+                    ops.append(("noise", DEPOLARIZE1, p_gate, np.ascontiguousarray(g[one, 1])))
+                if p_gate > 0 and two.any():
+                    ops.append(("noise", DEPOLARIZE2, p_gate,
+                                np.ascontiguousarray(g[two, 1:3].reshape(-1))))
+        elif op[0] == "measure":
+            if p_meas > 0 and len(op[1]):
+                ops.append(("noise", NOISE_X, p_meas, np.unique(np.asarray(op[1], np.uint32))))
+            ops.append(op)
+        else:
+            ops.append(op)
+    return Circuit(n=circ.n, gates=circ.gates, layer_ptr=circ.layer_ptr, ops=ops,
+                   name=(circ.name + f"_noise{p_gate:g}") if circ.name else "")
