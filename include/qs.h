@@ -189,12 +189,47 @@ uint64_t qs_sim_num_measurements(const qs_sim *sim);
 /* Copies record entries [first, first + count) to host bytes (0/1). Syncs. */
 int qs_sim_record(qs_sim *sim, uint64_t first, uint64_t count, uint8_t *dst);
 
+/* Pauli noise channels of qs_sim_noise (the values are part of the ABI). */
+enum {
+  QS_NOISE_X = 0,           /* X with probability p */
+  QS_NOISE_Y = 1,           /* Y with probability p */
+  QS_NOISE_Z = 2,           /* Z with probability p */
+  QS_NOISE_DEPOLARIZE1 = 3, /* X, Y or Z, each with probability p/3 */
+  QS_NOISE_DEPOLARIZE2 = 4, /* one of the 15 non-identity two-qubit Paulis, each p/15 */
+  QS_NUM_NOISE_KINDS = 5
+};
+
+/*
+ * Appends a Pauli noise channel to the sim's op log. Noise acts on the shots
+ * qs_sim_sample draws, through the Pauli frames (Sec. 3: frames carry error
+ * events as well as measurement randomness, so one noiseless reference shot
+ * serves every noisy shot); the tableau and the single-shot record are not
+ * touched. The paper fixes no channel set; these are the usual ones.
+ *   kind:    QS_NOISE_*.
+ *   p:       probability in [0, 1].
+ *   targets: host array of count qubits (< n, pairwise distinct); for
+ *            QS_NOISE_DEPOLARIZE2, count is even and targets hold pairs
+ *            (targets[2i], targets[2i+1]). Copied before the call returns.
+ * Randomness: noise op e (numbered from 0 in the op log) draws, for target i
+ * (pair i for DEPOLARIZE2) and shot s, the words (u, v) = words (2h, 2h + 1)
+ * of Philox4x64-10(counter = (e, i, 32 (s >> 6) + (s & 31), 3),
+ * key = (seed, 0xE5505)) with h = (s >> 5) & 1. The channel fires iff p >= 1
+ * or u < floor(p * 2^64); DEPOLARIZE1 then applies Pauli 1 + floor(3 v / 2^64)
+ * (1 = X, 2 = Y, 3 = Z) and DEPOLARIZE2 the pair with index
+ * 1 + floor(15 v / 2^64) = 4 a + b (0 = I, 1 = X, 2 = Y, 3 = Z on the first
+ * and second target).
+ * Errors: QS_ERR_ARG (unknown kind, p outside [0, 1] or NaN, a target >= n
+ * or repeated, odd count for DEPOLARIZE2). No device work.
+ */
+int qs_sim_noise(qs_sim *sim, int kind, double p, const uint32_t *targets, uint32_t count);
+
 /* Device bytes of frame workspace qs_sim_sample needs for `shots` shots. */
 size_t qs_sim_sample_required_bytes(const qs_sim *sim, uint64_t shots);
 
 /*
- * Samples `shots` shots of the program in the sim's op log (every layer and
- * measurement since create/reset) by Pauli frames (Sec. 5, Alg. 9): frames
+ * Samples `shots` shots of the program in the sim's op log (every layer,
+ * measurement and noise channel since create/reset) by Pauli frames (Sec. 5,
+ * Alg. 9): frames
  * start with X~ = 0, Z~ = keyed Philox words; gate layers act on the frames
  * without signs; measurement m of qubit q outputs X~[q] XOR ref[m] and
  * re-randomises Z~[q]. The reference ref is the sim's own single-shot record.

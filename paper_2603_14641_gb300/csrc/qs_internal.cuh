@@ -82,6 +82,7 @@ __device__ __forceinline__ P4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c
 
 constexpr uint64_t kCoinKey = 0x51A7Eull;
 constexpr uint64_t kFrameKey = 0xF4A3Eull;
+constexpr uint64_t kNoiseKey = 0xE5505ull;
 
 // ------------------------------------------------------------------------
 // Launchers (each returns cudaGetLastError() after the launch).
@@ -118,6 +119,13 @@ cudaError_t launch_frame_measure(uint64_t *FX, uint64_t *FZ, uint32_t n, uint32_
                                  const uint32_t *qubits, uint32_t count, uint64_t m0,
                                  const uint8_t *ref, uint64_t *out, uint64_t shots, uint64_t seed,
                                  uint32_t *err, cudaStream_t s);
+// noise op e (QS_NOISE_* kind) on targets[0..count) (pairs for DEPOLARIZE2,
+// count = number of pairs), global target index i0 + local index; shot words
+// 0..ow-1; fires iff always or u < thr
+cudaError_t launch_frame_noise(uint64_t *FX, uint64_t *FZ, uint32_t fw, uint32_t ow,
+                               const uint32_t *targets, uint32_t count, uint32_t i0, int kind,
+                               uint64_t thr, bool always, uint64_t e, uint64_t seed,
+                               cudaStream_t s);
 cudaError_t launch_reset_meas_state(const Dev &d, cudaStream_t s);
 // a window of measurements qubits[0..count) with record indices m0.., two
 // launches per measurement (plus two per window)

@@ -32,13 +32,17 @@ int fail(int code, const std::string &msg) {
 }
 
 struct Op {
-  enum Kind { kHostLayer, kDevLayers, kHostMeasure, kDevMeasure } kind;
+  enum Kind { kHostLayer, kDevLayers, kHostMeasure, kDevMeasure, kNoise } kind;
   std::vector<uint32_t> packed;  // kHostLayer: 2 words per gate
   const uint32_t *dev = nullptr; // kDevLayers: packed gates; kDevMeasure: qubit list
   std::vector<int64_t> ptr;      // kDevLayers: offsets of the replayed layers (+1)
-  std::vector<uint32_t> qubits;  // kHostMeasure
+  std::vector<uint32_t> qubits;  // kHostMeasure; kNoise: targets
   uint32_t count = 0;            // kDevMeasure
   uint64_t m0 = 0;               // first record index of a measurement op
+  int noise_kind = 0;            // kNoise: QS_NOISE_*
+  uint64_t thr = 0;              // kNoise: fires iff always or u < thr
+  bool always = false;
+  uint64_t ordinal = 0;          // kNoise: index among the noise ops (the draw's e)
 };
 
 constexpr int kRing = 4;
@@ -99,6 +103,7 @@ struct qs_sim {
   bool cols_valid = true, rows_valid = false;
   bool broken = false;
   uint64_t n_meas = 0;
+  uint64_t n_noise = 0;
   uint8_t *dstage = nullptr;
   uint8_t *hstage[kRing] = {};
   cudaEvent_t ev[kRing] = {};
@@ -351,6 +356,7 @@ int qs_sim_reset(qs_sim *s, const uint8_t *initstate) {
   s->cols_valid = true;
   s->rows_valid = false;
   s->n_meas = 0;
+  s->n_noise = 0;
   s->ops.clear();
   return QS_OK;
 }
@@ -527,6 +533,38 @@ int qs_sim_measure_dev(qs_sim *s, const uint32_t *qubits_dev, uint32_t count, qs
   return QS_OK;
 }
 
+int qs_sim_noise(qs_sim *s, int kind, double p, const uint32_t *targets, uint32_t count) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (kind < 0 || kind >= QS_NUM_NOISE_KINDS) return fail(QS_ERR_ARG, "unknown noise kind");
+  if (!(p >= 0.0 && p <= 1.0)) return fail(QS_ERR_ARG, "noise probability outside [0, 1]");
+  if (count && !targets) return fail(QS_ERR_ARG, "targets is NULL");
+  if (kind == QS_NOISE_DEPOLARIZE2 && (count & 1u))
+    return fail(QS_ERR_ARG, "DEPOLARIZE2 takes pairs of targets");
+  const uint32_t n = s->d.L.n;
+  if (s->stamp.size() < n) s->stamp.assign(n, 0);
+  if (++s->stamp_id == 0) {
+    std::fill(s->stamp.begin(), s->stamp.end(), 0);
+    s->stamp_id = 1;
+  }
+  for (uint32_t i = 0; i < count; ++i) {
+    if (targets[i] >= n) return fail(QS_ERR_ARG, "noise target " + std::to_string(targets[i]) + " >= n");
+    if (s->stamp[targets[i]] == s->stamp_id)
+      return fail(QS_ERR_ARG, "noise target " + std::to_string(targets[i]) + " repeated");
+    s->stamp[targets[i]] = s->stamp_id;
+  }
+  Op op;
+  op.kind = Op::kNoise;
+  op.noise_kind = kind;
+  op.qubits.assign(targets, targets + count);
+  op.always = p >= 1.0;
+  // floor(p * 2^64): multiplying by a power of two is exact
+  op.thr = op.always ? UINT64_MAX : (p > 0.0 ? (uint64_t)(p * 18446744073709551616.0) : 0);
+  op.ordinal = s->n_noise++;
+  s->ops.push_back(std::move(op));
+  return QS_OK;
+}
+
 uint64_t qs_sim_num_measurements(const qs_sim *s) { return s ? s->n_meas : 0; }
 
 uint64_t qs_sim_launch_count(const qs_sim *s) { return s ? s->launches : 0; }
@@ -557,6 +595,29 @@ int qs_sim_sync(qs_sim *s) {
     snprintf(buf, sizeof buf, "device self-check failed (flags 0x%x: odd phase=1, det=2, gate=4, qubit=8)",
              flags);
     return fail(QS_ERR_INTERNAL, buf);
+  }
+  return QS_OK;
+}
+
+// Replays a noise op on the frames: targets staged through the pinned ring in
+// chunks (whole pairs for DEPOLARIZE2), target index continued across chunks.
+static int replay_noise(qs_sim *s, const Op &op, uint64_t *FX, uint64_t *FZ, uint32_t fw, uint32_t ow,
+                        uint64_t seed) {
+  const bool pairs = op.noise_kind == QS_NOISE_DEPOLARIZE2;
+  const uint32_t per = pairs ? 2 : 1;
+  const uint32_t total = (uint32_t)op.qubits.size() / per;  // targets or pairs
+  const uint32_t chunk = (uint32_t)(s->plan.stage_bytes / 4 / per);
+  for (uint32_t t0 = 0; t0 < total; t0 += chunk) {
+    const uint32_t c = std::min(chunk, total - t0);
+    int slot;
+    uint8_t *h = ring_slot(s, &slot);
+    if (!h) return cuda_fail(s, cudaGetLastError(), "staging event");
+    memcpy(h, op.qubits.data() + (size_t)t0 * per, (size_t)c * per * 4);
+    int rc = upload(s, slot, (size_t)c * per * 4);
+    if (rc) return rc;
+    QS_CUDA(s, launch_frame_noise(FX, FZ, fw, ow, reinterpret_cast<uint32_t *>(s->dstage), c, t0,
+                                  op.noise_kind, op.thr, op.always, op.ordinal, seed, s->stream));
+    if (op.always || op.thr) s->launches += 1;
   }
   return QS_OK;
 }
@@ -631,6 +692,8 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
       if ((rc = run_dev_layers(s, FX, FZ, nullptr, (uint32_t)fw, op.dev, op.ptr.data(),
                                op.ptr.size() - 1, false)))
         return rc;
+    } else if (op.kind == Op::kNoise) {
+      if ((rc = replay_noise(s, op, FX, FZ, (uint32_t)fw, (uint32_t)ow, seed))) return rc;
     } else {
       // measurement window: split into runs of distinct qubits (Sec. 5 processes
       // the measurements of one window in parallel)
@@ -821,6 +884,8 @@ extern "C" int qs_sim_sample_noalloc(qs_sim *s, uint64_t shots, uint64_t seed, u
                                       s->d.err, s->stream));
         if (cnt) s->launches += 1;
       }
+    } else if (op.kind == Op::kNoise) {
+      if ((rc = replay_noise(s, op, FX, FZ, (uint32_t)fw, (uint32_t)ow, seed))) return rc;
     } else if (op.kind == Op::kDevMeasure) {
       // the list stays on the device: one launch per measurement keeps repeated
       // qubits in program order without reading the list back

@@ -24,6 +24,8 @@ QS_LAYOUT_ROWS_PACKED = 0
 
 GATES = dict(I=0, X=1, Y=2, Z=3, H=4, S=5, SDG=6, CX=7, CY=8, CZ=9, SWAP=10, ISWAP=11)
 QS_MEASURE = 12
+# Pauli noise channels of qs_sim_noise (frames only)
+QS_NOISE_X, QS_NOISE_Y, QS_NOISE_Z, QS_NOISE_DEPOLARIZE1, QS_NOISE_DEPOLARIZE2 = range(5)
 
 
 class QsError(RuntimeError):
@@ -80,6 +82,7 @@ SIGNATURES = {
     "qs_sim_apply_layers_dev": (ctypes.c_int, [_vp, _vp, _vp, _u32, _u32]),
     "qs_sim_measure": (ctypes.c_int, [_vp, _vp, _u32, qs_key, _vp]),
     "qs_sim_measure_dev": (ctypes.c_int, [_vp, _vp, _u32, qs_key]),
+    "qs_sim_noise": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _vp, _u32]),
     "qs_sim_num_measurements": (_u64, [_vp]),
     "qs_sim_record": (ctypes.c_int, [_vp, _u64, _u64, _vp]),
     "qs_sim_sample_required_bytes": (_sz, [_vp, _u64]),
@@ -209,6 +212,12 @@ def qs_sim_measure(sim: int, qubits: np.ndarray, seed: int, shot: int = 0,
 def qs_sim_measure_dev(sim: int, qubits_dev: int, count: int, seed: int, shot: int = 0) -> None:
     _check(lib().qs_sim_measure_dev(ctypes.c_void_p(sim), ctypes.c_void_p(qubits_dev), count,
                                     qs_key(seed, shot)), "qs_sim_measure_dev")
+
+
+def qs_sim_noise(sim: int, kind: int, p: float, targets) -> None:
+    t = np.ascontiguousarray(targets, np.uint32)
+    _check(lib().qs_sim_noise(ctypes.c_void_p(sim), int(kind), float(p),
+                              _ptr(t) if len(t) else None, len(t)), "qs_sim_noise")
 
 
 def qs_sim_num_measurements(sim: int) -> int:
@@ -349,8 +358,13 @@ class Simulator:
         self._keep.append(qubits_dev)
         qs_sim_measure_dev(self.sim, qubits_dev.data_ptr(), qubits_dev.numel(), seed, shot)
 
+    def noise(self, kind: int, p: float, targets):
+        """Appends a Pauli noise channel (QS_NOISE_*) for the sampled shots."""
+        qs_sim_noise(self.sim, kind, p, targets)
+
     def run(self, circuit, seed: int, shot: int = 0, dc: Optional[DeviceCircuit] = None):
-        """Runs circuit.ops; layers from host (or from `dc` if given). Returns the record."""
+        """Runs circuit.ops; layers from host (or from `dc` if given); noise ops
+        go to the op log for sample(). Returns the record."""
         for op in circuit.ops:
             if op[0] == "layers":
                 if dc is not None:
@@ -358,6 +372,8 @@ class Simulator:
                 else:
                     for l in range(op[1], op[2]):
                         self.apply_layer(circuit.layer(l))
+            elif op[0] == "noise":
+                self.noise(op[1], op[2], op[3])
             else:
                 self.measure(op[1], seed, shot, want_outcomes=False)
         return self.record()
@@ -419,6 +435,8 @@ def circuit_rounds(circuit):
                 raise ValueError("layer runs must be contiguous")
             cur_l = op[2]
             pending = True
+        elif op[0] == "noise":
+            continue  # noise acts on sampled shots only; the batch runs the reference shot
         else:
             qs_.append(np.asarray(op[1], np.uint32))
             cur_m += len(op[1])

@@ -190,6 +190,8 @@ class GpuExecutor:
             for op in c.ops:
                 if op[0] == "layers":
                     qs.qs_sim_apply_layers_dev(sim.sim, gates.data_ptr(), lp, op[1], op[2])
+                elif op[0] == "noise":
+                    qs.qs_sim_noise(sim.sim, op[1], op[2], op[3])
                 else:
                     q = torch.from_numpy(np.asarray(op[1], np.uint32).view(np.int32)).pin_memory()
                     qd = q.to(self.device, non_blocking=True)

@@ -46,6 +46,16 @@ def test_gate_codes_match_input_format():
         assert int(m.group(1)) == getattr(C, name) == qs.GATES[name]
 
 
+def test_noise_codes_match_input_format():
+    text = open(HEADER).read()
+    for name, hname in [("NOISE_X", "QS_NOISE_X"), ("NOISE_Y", "QS_NOISE_Y"), ("NOISE_Z", "QS_NOISE_Z"),
+                        ("DEPOLARIZE1", "QS_NOISE_DEPOLARIZE1"),
+                        ("DEPOLARIZE2", "QS_NOISE_DEPOLARIZE2")]:
+        m = re.search(rf"{hname}\s*=\s*(\d+)", text)
+        assert m, hname
+        assert int(m.group(1)) == getattr(C, name) == getattr(qs, hname)
+
+
 def test_version_and_required_bytes():
     assert "sm_103a" in qs.qs_version()
     n = 180_000
