@@ -210,14 +210,15 @@ enum {
  *   targets: host array of count qubits (< n, pairwise distinct); for
  *            QS_NOISE_DEPOLARIZE2, count is even and targets hold pairs
  *            (targets[2i], targets[2i+1]). Copied before the call returns.
- * Randomness: noise op e (numbered from 0 in the op log) draws, for target i
- * (pair i for DEPOLARIZE2) and shot s, the words (u, v) = words (2h, 2h + 1)
- * of Philox4x64-10(counter = (e, i, 32 (s >> 6) + (s & 31), 3),
- * key = (seed, 0xE5505)) with h = (s >> 5) & 1. The channel fires iff p >= 1
- * or u < floor(p * 2^64); DEPOLARIZE1 then applies Pauli 1 + floor(3 v / 2^64)
- * (1 = X, 2 = Y, 3 = Z) and DEPOLARIZE2 the pair with index
- * 1 + floor(15 v / 2^64) = 4 a + b (0 = I, 1 = X, 2 = Y, 3 = Z on the first
- * and second target).
+ * Randomness: for target i (pair i for DEPOLARIZE2) of noise op e (numbered
+ * from 0 in the op log) and shot s, the channel fires iff p >= 1 or
+ * u < floor(p * 2^32), where bit 31 - k of u (k = 0..31) is bit (s & 63) of
+ * word (k & 3) of Philox4x64-10(counter = (e, i, 8 (s >> 6) + (k >> 2), 3),
+ * key = (seed, 0xE5505)). When it fires, v = word 0 of
+ * Philox4x64-10(counter = (e, i, s, 4), same key) picks the Pauli:
+ * DEPOLARIZE1 applies 1 + floor(3 v / 2^64) (1 = X, 2 = Y, 3 = Z) and
+ * DEPOLARIZE2 the pair with index 1 + floor(15 v / 2^64) = 4 a + b
+ * (0 = I, 1 = X, 2 = Y, 3 = Z on the first and second target).
  * Errors: QS_ERR_ARG (unknown kind, p outside [0, 1] or NaN, a target >= n
  * or repeated, odd count for DEPOLARIZE2). No device work.
  */

@@ -48,13 +48,16 @@
  *                                                     key=(seed, 0x51A7E))
  *   frame_word(seed, e, q, j) = word (j & 3) of Philox(ctr=(e, q, j >> 2, 1),
  *                                                     key=(seed, 0xF4A3E))
- *   noise_draw(seed, e, i, s) = words (2h, 2h + 1) = (u, v) of
- *       Philox(ctr=(e, i, 32 (s >> 6) + (s & 31), 3), key=(seed, 0xE5505)),
- *       h = (s >> 5) & 1, for target i of noise op e (ops numbered from 0 in
- *       program order) and shot s. The channel fires iff p >= 1 or
- *       u < floor(p * 2^64); the Pauli is picked by floor(v * 3 / 2^64)
- *       (X, Y, Z) or floor(v * 15 / 2^64) + 1 (two-qubit Pauli index
- *       4 a + b with 0 = I, 1 = X, 2 = Y, 3 = Z).
+ *   noise_u(seed, e, i, s)  = the 32-bit number whose bit 31 - k is bit
+ *       (s & 63) of W_k, k = 0..31, W_k = word (k & 3) of
+ *       Philox(ctr=(e, i, 8 (s >> 6) + (k >> 2), 3), key=(seed, 0xE5505))
+ *   noise_v(seed, e, i, s)  = word 0 of Philox(ctr=(e, i, s, 4),
+ *                                              key=(seed, 0xE5505))
+ *       for target i of noise op e (ops numbered from 0 in program order)
+ *       and shot s. The channel fires iff p >= 1 or u < floor(p * 2^32);
+ *       when it fires, the Pauli is 1 + floor(3 v / 2^64) (1 = X, 2 = Y,
+ *       3 = Z) for DEPOLARIZE1, or the two-qubit Pauli with index
+ *       1 + floor(15 v / 2^64) = 4 a + b (0 = I, 1 = X, 2 = Y, 3 = Z).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -101,18 +104,25 @@ uint64_t oracle_frame_word(uint64_t seed, uint64_t e, uint64_t q, uint64_t j) {
 }
 
 void oracle_noise_draw(uint64_t seed, uint64_t e, uint64_t i, uint64_t s, uint64_t *u, uint64_t *v) {
-  uint64_t j = s >> 6, b = s & 63u, half = b >> 5;
-  uint64_t ctr[4] = {e, i, 32u * j + (b & 31u), 3}, key[2] = {seed, 0xE5505ull}, out[4];
-  oracle_philox4x64_10(ctr, key, out);
-  *u = out[2 * half];
-  *v = out[2 * half + 1];
+  uint64_t key[2] = {seed, 0xE5505ull}, out[4];
+  uint64_t j = s >> 6, b = s & 63u, acc = 0;
+  for (int t = 0; t < 8; ++t) { /* block t holds W_{4t} .. W_{4t+3} */
+    uint64_t cu[4] = {e, i, 8u * j + (uint64_t)t, 3};
+    oracle_philox4x64_10(cu, key, out);
+    for (int q = 0; q < 4; ++q) acc |= ((out[q] >> b) & 1u) << (31 - (4 * t + q));
+  }
+  *u = acc;
+  uint64_t cv[4] = {e, i, s, 4};
+  oracle_philox4x64_10(cv, key, out);
+  *v = out[0];
 }
 
-/* floor(p * 2^64) for 0 <= p < 1 (multiplying by a power of two is exact) */
+/* floor(p * 2^32) for 0 <= p < 1 (multiplying by a power of two is exact);
+ * 0 for p <= 0 and 2^32 for p >= 1 */
 uint64_t oracle_noise_threshold(double p) {
   if (!(p > 0.0)) return 0;
-  if (p >= 1.0) return UINT64_MAX;
-  return (uint64_t)(p * 18446744073709551616.0);
+  if (p >= 1.0) return 4294967296ull;
+  return (uint64_t)(p * 4294967296.0);
 }
 
 /* floor(v * k / 2^64): the high word of the 128-bit product */
@@ -400,7 +410,7 @@ static void frame_noise(uint8_t *fx, uint8_t *fz, int kind, double p, const uint
   for (long i = 0; i < targets; ++i) {
     uint64_t u, v;
     oracle_noise_draw(seed, e, (uint64_t)i, s, &u, &v);
-    int fire = p >= 1.0 || u < thr;
+    int fire = u < thr; /* thr = 2^32 when p >= 1 */
     if (!fire) continue;
     switch (kind) {
       case N_X: frame_pauli(fx, fz, (int)t[i], 1); break;

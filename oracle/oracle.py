@@ -234,14 +234,15 @@ def run_circuit(circuit, seed: int, shot: int = 0, force_zero: bool = False,
 
 
 def noise_draw(seed: int, e: int, i: int, s: int):
-    """(u, v) random words of target i of noise op e in shot s."""
+    """(u, v) draws of target i of noise op e in shot s: u (32 bits) decides
+    whether the channel fires, v (64 bits) picks the Pauli."""
     u, v = ctypes.c_uint64(), ctypes.c_uint64()
     lib().oracle_noise_draw(seed, e, i, s, ctypes.byref(u), ctypes.byref(v))
     return u.value, v.value
 
 
 def noise_threshold(p: float) -> int:
-    """floor(p * 2^64) for 0 <= p < 1 (0 for p <= 0, 2^64 - 1 for p >= 1)."""
+    """floor(p * 2^32) for 0 <= p < 1 (0 for p <= 0, 2^32 for p >= 1)."""
     return int(lib().oracle_noise_threshold(p))
 
 

@@ -10,10 +10,13 @@
 //                             Z~[q][j] = word (j & 3) of Philox(ctr = (m + 1, q, j >> 2, 1), ...).
 // The XOR with the reference record is the reading of Alg. 9 that makes the
 // output a sample (the frames carry flips relative to one valid record).
-//   Noise (frames carry error events, Sec. 3): target i of noise op e in
-//                             shot s draws (u, v) = words (2h, 2h + 1) of
-//                             Philox(ctr = (e, i, 32 (s >> 6) + (s & 31), 3),
-//                             key = (seed, 0xE5505)), h = (s >> 5) & 1.
+//   Noise (frames carry error events, Sec. 3): target i of noise op e fires
+//                             in shot s iff u < floor(p 2^32); bit 31 - k of u
+//                             is bit (s & 63) of word (k & 3) of
+//                             Philox(ctr = (e, i, 8 (s >> 6) + (k >> 2), 3),
+//                             key = (seed, 0xE5505));
+//                             the Pauli of a depolarising channel comes from
+//                             word 0 of Philox(ctr = (e, i, s, 4), same key).
 #include "qs_internal.cuh"
 
 namespace qs {
@@ -92,65 +95,89 @@ cudaError_t launch_frame_measure(uint64_t *FX, uint64_t *FZ, uint32_t n, uint32_
 }
 
 // Pauli noise channels on the frames (X_ERROR, Y_ERROR, Z_ERROR, DEPOLARIZE1,
-// DEPOLARIZE2; frames carry error events, Sec. 3). One warp per (target, shot
-// word j): lane l draws shots 64 j + l and 64 j + 32 + l from one Philox
-// block, words (0, 1) and (2, 3) = (u, v) of each, and the warp assembles the
-// 64-shot flip words with ballots. Targets of one op are distinct, so every
+// DEPOLARIZE2; frames carry error events, Sec. 3). One thread per (target,
+// shot word j). The 64 shots' 32-bit draws u are bit-sliced: bit 31 - k of
+// every shot's u sits in random word W_k, so u < thr is decided for all 64
+// shots at once from the most significant bit down, and the loop stops as
+// soon as no shot is undecided (about 8 words on average instead of 32).
+// The fire mask applies X/Y/Z directly; only the shots that fired draw the
+// Pauli of a depolarising channel. Targets of one op are distinct, so every
 // frame word has one writer.
-__device__ __forceinline__ int noise_code(int kind, uint64_t v) {
-  // Pauli code 1 = X, 2 = Y, 3 = Z of a one-qubit channel that fired
-  if (kind == QS_NOISE_DEPOLARIZE1) return 1 + (int)__umul64hi(v, 3);
-  return kind == QS_NOISE_X ? 1 : kind == QS_NOISE_Y ? 2 : 3;
+__device__ __forceinline__ uint64_t noise_v(uint64_t e, uint64_t i, uint64_t s, uint64_t seed) {
+  return philox4x64_10(e, i, s, 4, seed, kNoiseKey).v[0];
 }
-__device__ __forceinline__ uint64_t ballot64(bool lo, bool hi) {
-  return (uint64_t)__ballot_sync(0xffffffffu, lo) | ((uint64_t)__ballot_sync(0xffffffffu, hi) << 32);
+__device__ __forceinline__ void add_pauli(int code, uint64_t bit, uint64_t &mx, uint64_t &mz) {
+  if (code == 1 || code == 2) mx |= bit;
+  if (code == 2 || code == 3) mz |= bit;
 }
-__device__ __forceinline__ bool has_x(int c) { return c == 1 || c == 2; }
-__device__ __forceinline__ bool has_z(int c) { return c == 2 || c == 3; }
 
 __global__ void __launch_bounds__(256)
 frame_noise_kernel(uint64_t *__restrict__ FX, uint64_t *__restrict__ FZ, uint32_t fw, uint32_t ow,
                    const uint32_t *__restrict__ targets, uint32_t count, uint32_t i0, int kind,
-                   uint64_t thr, bool always, uint64_t e, uint64_t seed) {
-  const uint64_t wid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t lane = threadIdx.x & 31;
-  if (wid >= (uint64_t)count * ow) return;  // uniform over the warp
-  const uint32_t i = (uint32_t)(wid / ow), j = (uint32_t)(wid % ow);
-  const P4 r = philox4x64_10(e, i0 + i, 32ull * j + lane, 3, seed, kNoiseKey);
-  const bool f0 = always || r.v[0] < thr, f1 = always || r.v[2] < thr;
-  if (kind == QS_NOISE_DEPOLARIZE2) {
-    const int k0 = 1 + (int)__umul64hi(r.v[1], 15), k1 = 1 + (int)__umul64hi(r.v[3], 15);
-    const int a0 = f0 ? k0 >> 2 : 0, b0 = f0 ? k0 & 3 : 0, a1 = f1 ? k1 >> 2 : 0, b1 = f1 ? k1 & 3 : 0;
-    const uint64_t ax = ballot64(has_x(a0), has_x(a1)), az = ballot64(has_z(a0), has_z(a1));
-    const uint64_t bx = ballot64(has_x(b0), has_x(b1)), bz = ballot64(has_z(b0), has_z(b1));
-    if (lane == 0) {
-      const uint64_t qa = targets[2 * i], qb = targets[2 * i + 1];
-      if (ax) FX[qa * fw + j] ^= ax;
-      if (az) FZ[qa * fw + j] ^= az;
-      if (bx) FX[qb * fw + j] ^= bx;
-      if (bz) FZ[qb * fw + j] ^= bz;
-    }
+                   uint64_t thr, uint64_t e, uint64_t seed) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (uint64_t)count * ow) return;
+  const uint32_t i = (uint32_t)(tid / ow), j = (uint32_t)(tid % ow);
+  const uint64_t gi = (uint64_t)i0 + i;
+  uint64_t fire = 0;
+  if (thr >> 32) {
+    fire = ~0ull;  // p >= 1
   } else {
-    const int c0 = f0 ? noise_code(kind, r.v[1]) : 0, c1 = f1 ? noise_code(kind, r.v[3]) : 0;
-    const uint64_t mx = ballot64(has_x(c0), has_x(c1)), mz = ballot64(has_z(c0), has_z(c1));
-    if (lane == 0) {
-      const uint64_t q = targets[i];
-      if (mx) FX[q * fw + j] ^= mx;
-      if (mz) FZ[q * fw + j] ^= mz;
+    uint64_t undecided = ~0ull;
+    for (int t = 0; t < 8 && undecided; ++t) {
+      const P4 r = philox4x64_10(e, gi, 8ull * j + t, 3, seed, kNoiseKey);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint64_t w = r.v[q];  // bit 31 - (4 t + q) of every shot's u
+        if ((thr >> (31 - (4 * t + q))) & 1u) {
+          fire |= undecided & ~w;  // u has 0 where thr has 1: u < thr
+          undecided &= w;
+        } else {
+          undecided &= ~w;  // u has 1 where thr has 0: u > thr
+        }
+      }
     }
+    // shots still undecided after 32 bits have u == thr: no fire
+  }
+  if (!fire) return;
+  uint64_t ax = 0, az = 0, bx = 0, bz = 0;
+  if (kind == QS_NOISE_X) ax = fire;
+  else if (kind == QS_NOISE_Y) ax = az = fire;
+  else if (kind == QS_NOISE_Z) az = fire;
+  else {
+    uint64_t m = fire;
+    while (m) {
+      const int b = __ffsll((long long)m) - 1;
+      m &= m - 1;
+      const uint64_t v = noise_v(e, gi, 64ull * j + b, seed), bit = 1ull << b;
+      if (kind == QS_NOISE_DEPOLARIZE1) {
+        add_pauli(1 + (int)__umul64hi(v, 3), bit, ax, az);
+      } else {
+        const int idx = 1 + (int)__umul64hi(v, 15);
+        add_pauli(idx >> 2, bit, ax, az);
+        add_pauli(idx & 3, bit, bx, bz);
+      }
+    }
+  }
+  const uint64_t qa = kind == QS_NOISE_DEPOLARIZE2 ? targets[2 * i] : targets[i];
+  if (ax) FX[qa * fw + j] ^= ax;
+  if (az) FZ[qa * fw + j] ^= az;
+  if (kind == QS_NOISE_DEPOLARIZE2) {
+    const uint64_t qb = targets[2 * i + 1];
+    if (bx) FX[qb * fw + j] ^= bx;
+    if (bz) FZ[qb * fw + j] ^= bz;
   }
 }
 
 cudaError_t launch_frame_noise(uint64_t *FX, uint64_t *FZ, uint32_t fw, uint32_t ow,
                                const uint32_t *targets, uint32_t count, uint32_t i0, int kind,
-                               uint64_t thr, bool always, uint64_t e, uint64_t seed,
-                               cudaStream_t s) {
-  if (count == 0 || ow == 0 || (!always && thr == 0)) return cudaSuccess;  // never fires
-  const uint64_t warps = (uint64_t)count * ow;
-  const uint64_t blocks = (warps + 7) / 8;
+                               uint64_t thr, uint64_t e, uint64_t seed, cudaStream_t s) {
+  if (count == 0 || ow == 0 || thr == 0) return cudaSuccess;  // never fires
+  const uint64_t threads = (uint64_t)count * ow;
+  const uint64_t blocks = (threads + 255) / 256;
   if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidConfiguration;
   frame_noise_kernel<<<(unsigned)blocks, 256, 0, s>>>(FX, FZ, fw, ow, targets, count, i0, kind, thr,
-                                                      always, e, seed);
+                                                      e, seed);
   return cudaGetLastError();
 }
 

@@ -121,11 +121,10 @@ cudaError_t launch_frame_measure(uint64_t *FX, uint64_t *FZ, uint32_t n, uint32_
                                  uint32_t *err, cudaStream_t s);
 // noise op e (QS_NOISE_* kind) on targets[0..count) (pairs for DEPOLARIZE2,
 // count = number of pairs), global target index i0 + local index; shot words
-// 0..ow-1; fires iff always or u < thr
+// 0..ow-1; a shot fires iff its 32-bit draw u < thr (thr = 2^32: always)
 cudaError_t launch_frame_noise(uint64_t *FX, uint64_t *FZ, uint32_t fw, uint32_t ow,
                                const uint32_t *targets, uint32_t count, uint32_t i0, int kind,
-                               uint64_t thr, bool always, uint64_t e, uint64_t seed,
-                               cudaStream_t s);
+                               uint64_t thr, uint64_t e, uint64_t seed, cudaStream_t s);
 cudaError_t launch_reset_meas_state(const Dev &d, cudaStream_t s);
 // a window of measurements qubits[0..count) with record indices m0.., two
 // launches per measurement (plus two per window)

@@ -40,8 +40,7 @@ struct Op {
   uint32_t count = 0;            // kDevMeasure
   uint64_t m0 = 0;               // first record index of a measurement op
   int noise_kind = 0;            // kNoise: QS_NOISE_*
-  uint64_t thr = 0;              // kNoise: fires iff always or u < thr
-  bool always = false;
+  uint64_t thr = 0;              // kNoise: a shot fires iff its 32-bit draw u < thr
   uint64_t ordinal = 0;          // kNoise: index among the noise ops (the draw's e)
 };
 
@@ -557,9 +556,8 @@ int qs_sim_noise(qs_sim *s, int kind, double p, const uint32_t *targets, uint32_
   op.kind = Op::kNoise;
   op.noise_kind = kind;
   op.qubits.assign(targets, targets + count);
-  op.always = p >= 1.0;
-  // floor(p * 2^64): multiplying by a power of two is exact
-  op.thr = op.always ? UINT64_MAX : (p > 0.0 ? (uint64_t)(p * 18446744073709551616.0) : 0);
+  // floor(p * 2^32) (multiplying by a power of two is exact); 2^32 fires always
+  op.thr = p >= 1.0 ? 4294967296ull : (p > 0.0 ? (uint64_t)(p * 4294967296.0) : 0);
   op.ordinal = s->n_noise++;
   s->ops.push_back(std::move(op));
   return QS_OK;
@@ -616,8 +614,8 @@ static int replay_noise(qs_sim *s, const Op &op, uint64_t *FX, uint64_t *FZ, uin
     int rc = upload(s, slot, (size_t)c * per * 4);
     if (rc) return rc;
     QS_CUDA(s, launch_frame_noise(FX, FZ, fw, ow, reinterpret_cast<uint32_t *>(s->dstage), c, t0,
-                                  op.noise_kind, op.thr, op.always, op.ordinal, seed, s->stream));
-    if (op.always || op.thr) s->launches += 1;
+                                  op.noise_kind, op.thr, op.ordinal, seed, s->stream));
+    if (op.thr) s->launches += 1;
   }
   return QS_OK;
 }

@@ -100,7 +100,7 @@ MUTATIONS = [
     ("frames drop the reference record",
      "(uint8_t)(fx[q] ^ ref[m]);", "(uint8_t)(fx[q]);", _pins_frames),
     ("noise fires above the threshold",
-     "int fire = p >= 1.0 || u < thr;", "int fire = p >= 1.0 || u > thr;", _pins_noise),
+     "int fire = u < thr;", "int fire = u > thr;", _pins_noise),
     ("Y error flips only z",
      "if (code == 1 || code == 2) fx[q] ^= 1u;", "if (code == 1) fx[q] ^= 1u;", _pins_noise),
     ("DEPOLARIZE1 can pick the identity",

@@ -14,7 +14,7 @@ its header. Pinned here against things other than its own formulas:
   through H and CX as the conjugation rules say;
 - rates: the flip frequency of X_ERROR(p) and the single and joint flip
   frequencies of DEPOLARIZE1/2 (2/3, 8/15, 4/15 at p = 1) within 5 sigma;
-- the threshold is floor(p * 2^64) at exactly representable p, and the
+- the threshold is floor(p * 2^32) at exactly representable p, and the
   draws come from the Philox stream pinned against numpy in
   test_oracle_measure.py.
 """
@@ -252,16 +252,20 @@ def test_flip_rates():
 
 
 def test_threshold_and_draws():
-    assert O.noise_threshold(0.25) == 2 ** 62
-    assert O.noise_threshold(0.5) == 2 ** 63
-    assert O.noise_threshold(1 - 2.0 ** -53) == 2 ** 64 - 2 ** 11
+    assert O.noise_threshold(0.25) == 2 ** 30
+    assert O.noise_threshold(0.5) == 2 ** 31
+    assert O.noise_threshold(1 - 2.0 ** -53) == 2 ** 32 - 1
+    assert O.noise_threshold(1e-3) == 4294967  # floor(0.001 * 2^32)
     assert O.noise_threshold(0.0) == 0 and O.noise_threshold(-1.0) == 0
-    assert O.noise_threshold(1.0) == 2 ** 64 - 1
+    assert O.noise_threshold(1.0) == 2 ** 32
     for seed, e, i, s in [(1, 0, 0, 0), (5, 3, 7, 31), (5, 3, 7, 32), (9, 2**20, 99, 10**6 + 77)]:
         j, b = s >> 6, s & 63
-        blk = O.philox4x64_10((e, i, 32 * j + (b & 31), 3), (seed, 0xE5505))
-        h = b >> 5
-        assert O.noise_draw(seed, e, i, s) == (int(blk[2 * h]), int(blk[2 * h + 1]))
-    # a shot pair (s, s + 32) shares one Philox block; s and s + 64 do not
-    assert O.noise_draw(3, 1, 2, 5)[0] != O.noise_draw(3, 1, 2, 37)[0]
-    assert O.noise_draw(3, 1, 2, 5) != O.noise_draw(3, 1, 2, 69)
+        u = 0
+        for k in range(32):
+            w = int(O.philox4x64_10((e, i, 8 * j + (k >> 2), 3), (seed, 0xE5505))[k & 3])
+            u |= ((w >> b) & 1) << (31 - k)
+        v = int(O.philox4x64_10((e, i, s, 4), (seed, 0xE5505))[0])
+        assert O.noise_draw(seed, e, i, s) == (u, v)
+    # the 64 shots of a word take distinct bit columns of the same words
+    us = [O.noise_draw(3, 1, 2, s)[0] for s in range(64, 128)]
+    assert len(set(us)) == 64
