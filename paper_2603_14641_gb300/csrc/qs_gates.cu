@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "qs_internal.cuh"
+#include "qs_rules.cuh"
 
 namespace qs {
 
@@ -73,9 +74,81 @@ cudaError_t launch_init(const Dev &d, const uint8_t *initstate_dev, cudaStream_t
 //   packed[2 g] = type << 24 | q0, packed[2 g + 1] = q1
 //   block: P pair-threads x `lanes` gate lanes (P * lanes <= 256);
 //   grid.x: gate groups of `lanes * gpl` gates; grid.y: chunks of P pairs.
+// On the tableau a thread walks its gates two at a time: both gates' column
+// words are loaded before either is stored (the gates of a layer touch
+// disjoint columns), which doubles the bytes each thread keeps in flight -- at
+// one gate per thread the kernel is bound by memory latency x bytes in flight
+// (0.86 of the HBM peak at 180k qubits; 0.93 with two). Frames (short columns,
+// many gate lanes per block) keep one gate per thread.
 // ---------------------------------------------------------------------
+struct GateIn {
+  uint32_t type, qa, qb;
+  ulonglong2 x1, z1, x2, z2;
+};
+
+// Reads the record of gate g and the column words it needs; false for an
+// invalid record (flagged, skipped).
 template <bool SIGNS>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ bool gate_load(GateIn &in, uint32_t g, const uint32_t *__restrict__ packed,
+                                          uint64_t *X, uint64_t *Z, uint32_t n, uint32_t cs,
+                                          size_t off, bool flag, uint32_t *err) {
+  const uint32_t w0 = __ldg(packed + 2 * g), qb = __ldg(packed + 2 * g + 1);
+  const uint32_t type = w0 >> 24, qa = w0 & 0xFFFFFFu;
+  const bool two = is_two_qubit(type);
+  if (qa >= n || type >= QS_NUM_GATE_TYPES || (two && (qb >= n || qb == qa))) {
+    if (flag) atomicOr(err, kErrBadGate);
+    return false;
+  }
+  in.type = type;
+  in.qa = qa;
+  in.qb = qb;
+  const uint64_t *xa = X + (size_t)qa * cs + off, *za = Z + (size_t)qa * cs + off;
+  const uint64_t *xb = X + (size_t)qb * cs + off, *zb = Z + (size_t)qb * cs + off;
+  const ulonglong2 zero = make_ulonglong2(0, 0);
+  in.x1 = in.z1 = in.x2 = in.z2 = zero;
+  switch (type) {
+    case QS_X: if (SIGNS) in.z1 = ld2(za); break;
+    case QS_Z: if (SIGNS) in.x1 = ld2(xa); break;
+    case QS_Y: if (SIGNS) { in.x1 = ld2(xa); in.z1 = ld2(za); } break;
+    case QS_H: case QS_S: case QS_SDG: in.x1 = ld2(xa); in.z1 = ld2(za); break;
+    case QS_CX: case QS_CZ: case QS_CY: case QS_SWAP: case QS_ISWAP:
+      in.x1 = ld2(xa); in.z1 = ld2(za); in.x2 = ld2(xb); in.z2 = ld2(zb); break;
+    default: break;  // QS_I
+  }
+  return true;
+}
+
+// Applies the rules of qs_rules.cuh to both words and stores the columns the
+// gate changes.
+template <bool SIGNS>
+__device__ __forceinline__ void gate_apply(GateIn &in, ulonglong2 &sacc, uint64_t *X, uint64_t *Z,
+                                           uint32_t cs, size_t off) {
+  uint64_t *xa = X + (size_t)in.qa * cs + off, *za = Z + (size_t)in.qa * cs + off;
+  uint64_t *xb = X + (size_t)in.qb * cs + off, *zb = Z + (size_t)in.qb * cs + off;
+  uint64_t s0 = 0, s1 = 0;
+  uint64_t a0 = in.x1.x, b0 = in.z1.x, c0 = in.x2.x, d0 = in.z2.x;
+  uint64_t a1 = in.x1.y, b1 = in.z1.y, c1 = in.x2.y, d1 = in.z2.y;
+  rule<SIGNS>(in.type, a0, b0, c0, d0, s0);
+  rule<SIGNS>(in.type, a1, b1, c1, d1, s1);
+  in.x1 = make_ulonglong2(a0, a1);
+  in.z1 = make_ulonglong2(b0, b1);
+  in.x2 = make_ulonglong2(c0, c1);
+  in.z2 = make_ulonglong2(d0, d1);
+  if (SIGNS) { sacc.x ^= s0; sacc.y ^= s1; }
+  switch (in.type) {
+    case QS_H: st2(xa, in.x1); st2(za, in.z1); break;
+    case QS_S: case QS_SDG: st2(za, in.z1); break;
+    case QS_CX: st2(xb, in.x2); st2(za, in.z1); break;
+    case QS_CZ: st2(za, in.z1); st2(zb, in.z2); break;
+    case QS_CY: st2(za, in.z1); st2(xb, in.x2); st2(zb, in.z2); break;
+    case QS_SWAP: case QS_ISWAP:
+      st2(xa, in.x1); st2(za, in.z1); st2(xb, in.x2); st2(zb, in.z2); break;
+    default: break;  // I, X, Y, Z change signs only
+  }
+}
+
+template <bool SIGNS, int INFLIGHT>
+__global__ void __launch_bounds__(256, SIGNS ? 4 : 6)
 gate_layer_kernel(uint64_t *__restrict__ X, uint64_t *__restrict__ Z, uint64_t *__restrict__ S,
                   uint32_t n, uint32_t cs, const uint32_t *__restrict__ packed, uint32_t n_gates,
                   uint32_t P, uint32_t lanes, uint32_t gpl, uint32_t *__restrict__ err) {
@@ -91,95 +164,17 @@ gate_layer_kernel(uint64_t *__restrict__ X, uint64_t *__restrict__ Z, uint64_t *
 
   if (active) {
     const size_t off = 2 * (size_t)pair;
-    for (uint32_t g = g0 + lane; g < g1; g += lanes) {
-      const uint32_t w0 = __ldg(packed + 2 * g), qb = __ldg(packed + 2 * g + 1);
-      const uint32_t type = w0 >> 24, qa = w0 & 0xFFFFFFu;
-      const bool two = is_two_qubit(type);
-      if (qa >= n || type >= QS_NUM_GATE_TYPES || (two && (qb >= n || qb == qa))) {
-        if (pair == 0) atomicOr(err, kErrBadGate);
-        continue;
-      }
-      uint64_t *xa = X + (size_t)qa * cs + off;
-      uint64_t *za = Z + (size_t)qa * cs + off;
-      uint64_t *xb = X + (size_t)qb * cs + off;
-      uint64_t *zb = Z + (size_t)qb * cs + off;
-      switch (type) {
-        case QS_X:
-          if (SIGNS) { ulonglong2 z = ld2(za); sacc.x ^= z.x; sacc.y ^= z.y; }
-          break;
-        case QS_Z:
-          if (SIGNS) { ulonglong2 x = ld2(xa); sacc.x ^= x.x; sacc.y ^= x.y; }
-          break;
-        case QS_Y:
-          if (SIGNS) {
-            ulonglong2 x = ld2(xa), z = ld2(za);
-            sacc.x ^= x.x ^ z.x; sacc.y ^= x.y ^ z.y;
-          }
-          break;
-        case QS_H: {
-          ulonglong2 x = ld2(xa), z = ld2(za);
-          if (SIGNS) { sacc.x ^= x.x & z.x; sacc.y ^= x.y & z.y; }
-          st2(xa, z); st2(za, x);
-        } break;
-        case QS_S: {
-          ulonglong2 x = ld2(xa), z = ld2(za);
-          if (SIGNS) { sacc.x ^= x.x & z.x; sacc.y ^= x.y & z.y; }
-          st2(za, make_ulonglong2(z.x ^ x.x, z.y ^ x.y));
-        } break;
-        case QS_SDG: {
-          ulonglong2 x = ld2(xa), z = ld2(za);
-          if (SIGNS) { sacc.x ^= x.x & ~z.x; sacc.y ^= x.y & ~z.y; }
-          st2(za, make_ulonglong2(z.x ^ x.x, z.y ^ x.y));
-        } break;
-        case QS_CX: {  // control a, target b
-          ulonglong2 x1 = ld2(xa), z1 = ld2(za), x2 = ld2(xb), z2 = ld2(zb);
-          if (SIGNS) {
-            sacc.x ^= x1.x & z2.x & ~(x2.x ^ z1.x);
-            sacc.y ^= x1.y & z2.y & ~(x2.y ^ z1.y);
-          }
-          st2(xb, make_ulonglong2(x2.x ^ x1.x, x2.y ^ x1.y));
-          st2(za, make_ulonglong2(z1.x ^ z2.x, z1.y ^ z2.y));
-        } break;
-        case QS_CZ: {
-          ulonglong2 x1 = ld2(xa), z1 = ld2(za), x2 = ld2(xb), z2 = ld2(zb);
-          if (SIGNS) {
-            sacc.x ^= x1.x & x2.x & (z1.x ^ z2.x);
-            sacc.y ^= x1.y & x2.y & (z1.y ^ z2.y);
-          }
-          st2(za, make_ulonglong2(z1.x ^ x2.x, z1.y ^ x2.y));
-          st2(zb, make_ulonglong2(z2.x ^ x1.x, z2.y ^ x1.y));
-        } break;
-        case QS_CY: {  // S_b^dag, CX(a, b), S_b, all in registers
-          ulonglong2 x1 = ld2(xa), z1 = ld2(za), x2 = ld2(xb), z2 = ld2(zb);
-          uint64_t s0 = 0, s1 = 0;
-          s0 ^= x2.x & ~z2.x; s1 ^= x2.y & ~z2.y;
-          z2.x ^= x2.x; z2.y ^= x2.y;
-          s0 ^= x1.x & z2.x & ~(x2.x ^ z1.x); s1 ^= x1.y & z2.y & ~(x2.y ^ z1.y);
-          x2.x ^= x1.x; x2.y ^= x1.y; z1.x ^= z2.x; z1.y ^= z2.y;
-          s0 ^= x2.x & z2.x; s1 ^= x2.y & z2.y;
-          z2.x ^= x2.x; z2.y ^= x2.y;
-          if (SIGNS) { sacc.x ^= s0; sacc.y ^= s1; }
-          st2(za, z1); st2(xb, x2); st2(zb, z2);
-        } break;
-        case QS_SWAP: {
-          ulonglong2 x1 = ld2(xa), z1 = ld2(za), x2 = ld2(xb), z2 = ld2(zb);
-          st2(xa, x2); st2(za, z2); st2(xb, x1); st2(zb, z1);
-        } break;
-        case QS_ISWAP: {  // CZ, SWAP, S_a, S_b in circuit order
-          ulonglong2 x1 = ld2(xa), z1 = ld2(za), x2 = ld2(xb), z2 = ld2(zb);
-          uint64_t s0 = x1.x & x2.x & (z1.x ^ z2.x), s1 = x1.y & x2.y & (z1.y ^ z2.y);
-          ulonglong2 nz1 = make_ulonglong2(z1.x ^ x2.x, z1.y ^ x2.y);
-          ulonglong2 nz2 = make_ulonglong2(z2.x ^ x1.x, z2.y ^ x1.y);
-          // after SWAP: qubit a holds (x2, nz2), qubit b holds (x1, nz1)
-          s0 ^= x2.x & nz2.x; s1 ^= x2.y & nz2.y;
-          s0 ^= x1.x & nz1.x; s1 ^= x1.y & nz1.y;
-          if (SIGNS) { sacc.x ^= s0; sacc.y ^= s1; }
-          st2(xa, x2); st2(za, make_ulonglong2(nz2.x ^ x2.x, nz2.y ^ x2.y));
-          st2(xb, x1); st2(zb, make_ulonglong2(nz1.x ^ x1.x, nz1.y ^ x1.y));
-        } break;
-        default:
-          break;  // QS_I
-      }
+    const bool flag = pair == 0;
+    for (uint32_t g = g0 + lane; g < g1; g += INFLIGHT * lanes) {
+      GateIn in[INFLIGHT];
+      bool ok[INFLIGHT];
+#pragma unroll
+      for (int u = 0; u < INFLIGHT; ++u)
+        ok[u] = g + u * lanes < g1 &&
+                gate_load<SIGNS>(in[u], g + u * lanes, packed, X, Z, n, cs, off, flag, err);
+#pragma unroll
+      for (int u = 0; u < INFLIGHT; ++u)
+        if (ok[u]) gate_apply<SIGNS>(in[u], sacc, X, Z, cs, off);
     }
   }
   if (SIGNS) {
@@ -229,7 +224,7 @@ cudaError_t launch_gate_layer(const Dev &d, const uint32_t *packed, uint32_t n_g
                               cudaStream_t s) {
   if (n_gates == 0) return cudaSuccess;
   GateGrid g = gate_grid(d.L.cs / 2, n_gates);
-  gate_layer_kernel<true><<<g.grid, g.block, 0, s>>>(d.X, d.Z, d.S, d.L.n, d.L.cs, packed, n_gates,
+  gate_layer_kernel<true, 2><<<g.grid, g.block, 0, s>>>(d.X, d.Z, d.S, d.L.n, d.L.cs, packed, n_gates,
                                                      g.P, g.lanes, g.gpl, d.err);
   return cudaGetLastError();
 }
@@ -239,7 +234,7 @@ cudaError_t launch_frame_layer(uint64_t *FX, uint64_t *FZ, uint32_t n, uint32_t 
                                cudaStream_t s) {
   if (n_gates == 0) return cudaSuccess;
   GateGrid g = gate_grid(fw / 2, n_gates);
-  gate_layer_kernel<false><<<g.grid, g.block, 0, s>>>(FX, FZ, nullptr, n, fw, packed, n_gates, g.P,
+  gate_layer_kernel<false, 1><<<g.grid, g.block, 0, s>>>(FX, FZ, nullptr, n, fw, packed, n_gates, g.P,
                                                       g.lanes, g.gpl, err);
   return cudaGetLastError();
 }
