@@ -51,6 +51,7 @@ struct BlkState {
   int32_t Cp[64];      // parity of (z_V ^ z_orig) . x_orig
   int32_t rV[64];      // sign bit of V_j
   uint64_t G[64];      // G[s] bit t = parity(z_{V_s} . x_{V_t})
+  uint64_t cpiv[64];   // C of the pivot row at its step (one-CTA symbolic pass)
   uint32_t err;
 };
 
@@ -148,6 +149,90 @@ blk_step_kernel(uint64_t nrows, uint32_t n, uint32_t k, int j, int B, const uint
       }
     }
   }
+}
+
+// Symbolic pass in one CTA when the C words of the n stabilizer rows fit in
+// shared memory (n <= kSymSmallRows): after blk_init_kernel, the same result
+// as B blk_step_kernel launches. Only stabilizer rows can be pivots, so the
+// step loop tracks only their C words: each step finds the pivot with a
+// block-wide min and XORs the pivot's C into the stabilizer targets. Every
+// row's M_r and base_r then follow from replaying the recorded pivots
+// (p_j, C_{p_j}) on its original C (blk_replay_kernel, one thread per row).
+constexpr uint32_t kSymSmallRows = 25600;  // 200 KB of C words
+constexpr int kSymThreads = 1024;
+
+__global__ void __launch_bounds__(kSymThreads)
+blk_symbolic_small_kernel(uint32_t n, uint32_t k, int B, const uint64_t *__restrict__ C0,
+                          BlkState *st) {
+  extern __shared__ uint64_t sc[];  // [n]: C of stabilizer row 64 k + i
+  __shared__ uint32_t swarp[kSymThreads / 32];
+  __shared__ uint32_t sbest;
+  __shared__ uint64_t scp;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t lo = 64ull * k;
+  for (uint32_t i = tid; i < n; i += kSymThreads) sc[i] = C0[lo + i];
+  __syncthreads();
+  int len = B;
+  for (int j = 0; j < B; ++j) {
+    // pivot: smallest stabilizer row with bit j set (a thread's rows ascend)
+    uint32_t best = 0xFFFFFFFFu;
+    for (uint32_t i = tid; i < n; i += kSymThreads)
+      if ((sc[i] >> j) & 1ull) { best = i; break; }
+    best = __reduce_min_sync(0xffffffffu, best);
+    if (lane == 0) swarp[warp] = best;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t v = lane < kSymThreads / 32 ? swarp[lane] : 0xFFFFFFFFu;
+      v = __reduce_min_sync(0xffffffffu, v);
+      if (lane == 0) {
+        sbest = v;
+        if (v != 0xFFFFFFFFu) {
+          scp = sc[v];
+          st->piv[j] = (int64_t)(lo + v);
+          st->cpiv[j] = sc[v];
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t b = sbest;
+    if (b == 0xFFFFFFFFu) { len = j; break; }  // deterministic: the block ends before step j
+    const uint64_t cp = scp;
+    for (uint32_t i = tid; i < n; i += kSymThreads) {
+      const uint64_t c = sc[i];
+      if (i == b) sc[i] = 0;
+      else if ((c >> j) & 1ull) sc[i] = c ^ cp;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) st->len = len;
+}
+
+__global__ void __launch_bounds__(256)
+blk_replay_kernel(uint64_t nrows, uint32_t k, const uint64_t *__restrict__ C0,
+                  uint64_t *__restrict__ M, int32_t *__restrict__ base, BlkState *st) {
+  const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const int L = st->len;
+  const int64_t lo = 64ll * k;
+  uint64_t c = C0[r], m = 0;
+  int32_t b = kBaseOrig;
+  for (int j = 0; j < L; ++j) {
+    const int64_t p = st->piv[j];
+    if ((int64_t)r == p) {
+      st->mpiv[j] = m;
+      b = kBasePivot + j;
+      c = 0;
+    } else if ((int64_t)r == p - lo) {
+      c = st->cpiv[j];
+      m = 0;
+      b = j;
+    } else if ((c >> j) & 1ull) {
+      c ^= st->cpiv[j];
+      m |= 1ull << j;
+    }
+  }
+  M[r] = m;
+  base[r] = b;
 }
 
 // pivot rows V_j and their phase sums for one chunk of 32 column words.
@@ -537,12 +622,6 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   uint64_t *VZ = reinterpret_cast<uint64_t *>(take(64ull * L.rs * 8));
   BlkState *st = reinterpret_cast<BlkState *>(take(sizeof(BlkState)));
   const unsigned rb = (unsigned)((L.nrows + 255) / 256);
-  blk_reset_kernel<<<1, 64, 0, s>>>(st, B);
-  blk_init_kernel<<<rb, 256, 0, s>>>(d.RX, L.rs, L.nrows, L.n, L.k, qubits, B, C0, M, base, st,
-                                     d.err);
-  for (int j = 0; j < B; ++j)
-    blk_step_kernel<<<rb, 256, 0, s>>>(L.nrows, L.n, L.k, j, B, (j & 1) ? C1 : C0,
-                                       (j & 1) ? C0 : C1, M, base, st);
   const size_t smem = (size_t)kEntries * kEntryBytes;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -555,8 +634,25 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(blk_vrows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kVrowSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(blk_symbolic_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kSymSmallRows * sizeof(uint64_t)));
     if (e != cudaSuccess) return e;
     g_apply_attr_set |= 1ull << dev;
+  }
+  blk_reset_kernel<<<1, 64, 0, s>>>(st, B);
+  blk_init_kernel<<<rb, 256, 0, s>>>(d.RX, L.rs, L.nrows, L.n, L.k, qubits, B, C0, M, base, st,
+                                     d.err);
+  int sym_launches = B;
+  if (L.n <= kSymSmallRows) {
+    blk_symbolic_small_kernel<<<1, kSymThreads, (size_t)L.n * sizeof(uint64_t), s>>>(L.n, L.k, B, C0,
+                                                                                     st);
+    blk_replay_kernel<<<rb, 256, 0, s>>>(L.nrows, L.k, C0, M, base, st);
+    sym_launches = 2;
+  } else {
+    for (int j = 0; j < B; ++j)
+      blk_step_kernel<<<rb, 256, 0, s>>>(L.nrows, L.n, L.k, j, B, (j & 1) ? C1 : C0,
+                                         (j & 1) ? C0 : C1, M, base, st);
   }
   blk_vrows_kernel<<<chunks, kVrowThreads, kVrowSmem, s>>>(d.RX, d.RZ, L.rs, VX, VZ, st);
   blk_signs_kernel<<<1, 64, 0, s>>>(d.S, st, d.err);
@@ -571,7 +667,7 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
         d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, M, base, Tp, st);
   blk_rows_kernel<<<rb, 256, 0, s>>>(d.S, L.nrows, qubits, M, base, Tp, chunks, st, m0, key.seed,
                                      key.shot, d.record, d.err);
-  if (launches) *launches += 6 + B;
+  if (launches) *launches += 6 + sym_launches;
   if (len_dev) *len_dev = &st->len;
   return cudaGetLastError();
 }
