@@ -78,8 +78,8 @@ cudaError_t launch_init(const Dev &d, const uint8_t *initstate_dev, cudaStream_t
 // words are loaded before either is stored (the gates of a layer touch
 // disjoint columns), which doubles the bytes each thread keeps in flight -- at
 // one gate per thread the kernel is bound by memory latency x bytes in flight
-// (0.86 of the HBM peak at 180k qubits; 0.93 with two). Frames (short columns,
-// many gate lanes per block) keep one gate per thread.
+// (0.87 of the HBM peak at 180k qubits; 0.97 with two). Frames with short
+// columns (many gate lanes per block) keep one gate per thread.
 // ---------------------------------------------------------------------
 struct GateIn {
   uint32_t type, qa, qb;
@@ -148,7 +148,7 @@ __device__ __forceinline__ void gate_apply(GateIn &in, ulonglong2 &sacc, uint64_
 }
 
 template <bool SIGNS, int INFLIGHT>
-__global__ void __launch_bounds__(256, SIGNS ? 4 : 6)
+__global__ void __launch_bounds__(256, INFLIGHT == 2 ? 4 : 6)
 gate_layer_kernel(uint64_t *__restrict__ X, uint64_t *__restrict__ Z, uint64_t *__restrict__ S,
                   uint32_t n, uint32_t cs, const uint32_t *__restrict__ packed, uint32_t n_gates,
                   uint32_t P, uint32_t lanes, uint32_t gpl, uint32_t *__restrict__ err) {
@@ -234,8 +234,12 @@ cudaError_t launch_frame_layer(uint64_t *FX, uint64_t *FZ, uint32_t n, uint32_t 
                                cudaStream_t s) {
   if (n_gates == 0) return cudaSuccess;
   GateGrid g = gate_grid(fw / 2, n_gates);
-  gate_layer_kernel<false, 1><<<g.grid, g.block, 0, s>>>(FX, FZ, nullptr, n, fw, packed, n_gates, g.P,
-                                                      g.lanes, g.gpl, err);
+  if (g.lanes == 1)  // long frame columns (>= 512 shot words): as the tableau, two gates in flight
+    gate_layer_kernel<false, 2><<<g.grid, g.block, 0, s>>>(FX, FZ, nullptr, n, fw, packed, n_gates,
+                                                        g.P, g.lanes, g.gpl, err);
+  else
+    gate_layer_kernel<false, 1><<<g.grid, g.block, 0, s>>>(FX, FZ, nullptr, n, fw, packed, n_gates,
+                                                        g.P, g.lanes, g.gpl, err);
   return cudaGetLastError();
 }
 

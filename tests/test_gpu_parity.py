@@ -163,6 +163,19 @@ def test_frames_bit_exact(n, shots):
     assert np.array_equal(words_dev, words)
 
 
+def test_frames_bit_exact_long_columns():
+    """33,000 shots: frame columns of 516 words take the two-gates-in-flight
+    frame kernel."""
+    circ = C.gate_mix_circuit(37, 10, seed=12, measure_every=3, measure_frac=0.4)
+    sim = _sim(37)
+    rec = sim.run(circ, seed=5)
+    shots = 33_000
+    words = sim.sample(shots, seed=8, on_device=False)
+    bits = np.unpackbits(words.view(np.uint8), axis=1, bitorder="little")
+    assert not bits[:, shots:].any()
+    assert np.array_equal(bits[:, :shots], O.frames(circ, rec, shots, seed=8))
+
+
 def test_frames_device_resident_replay():
     circ = C.random_circuit(400, 20, 0.5, seed=8, measure_every=5, measure_frac=0.1)
     sim = _sim(circ.n)
