@@ -308,7 +308,14 @@ int qs_sim_sample_noalloc(qs_sim *sim, uint64_t shots, uint64_t seed, uint64_t *
  * The coin of the circuit's m-th measurement (program order) is keyed by
  * (seed, shot, m) exactly as in qs_sim_measure, so a circuit's record and
  * tableau are the same alone (qs_sim_*) and in a batch. All arrays are host
- * memory and are copied at qs_batch_create. n <= 8192.
+ * memory and are copied at qs_batch_create. 1 <= n <= 2^20.
+ *
+ * Circuits of n < 1024 qubits run in one cooperative persistent kernel on the
+ * batch's stream (their cost is per-launch overhead when they run alone);
+ * circuits of n >= 1024 run through one qs_sim each (blocked measurement),
+ * spread over up to 16 worker streams that host threads drive during
+ * qs_batch_run. The paper has no batch mode; this follows the batched
+ * workload's shape (many small and some large circuits).
  */
 typedef struct qs_batch_circuit {
   uint32_t n;
@@ -340,20 +347,26 @@ typedef struct qs_batch_tuning {
 
 typedef struct qs_batch qs_batch;
 
-/* Device bytes of a batch (0 if the description is invalid). */
+/* Device bytes of a batch's persistent-kernel part (0 if the description is
+ * invalid); the simulators of the n >= 1024 circuits allocate their own. */
 size_t qs_batch_required_bytes(uint32_t count, const qs_batch_circuit *circuits);
 
 /* Validates (as qs_pack_layers; measured qubits < n; offsets in range) and
  * uploads the batch. workspace: caller device memory of >= required bytes,
- * 256-byte aligned, or NULL to let the library cudaMalloc it. */
+ * 256-byte aligned, or NULL to let the library cudaMalloc it. Creates the
+ * worker streams and the simulators of the n >= 1024 circuits. */
 int qs_batch_create(uint32_t count, const qs_batch_circuit *circuits, void *cuda_stream,
                     void *workspace, size_t workspace_bytes, qs_batch **out);
 
 int qs_batch_destroy(qs_batch *batch);
 
 /* Runs every circuit from |0...0> through its rounds (the first round_limit
- * rounds, 0 = all) in one cooperative persistent kernel launch on the
- * batch's stream. tuning: NULL for the default shape. Asynchronous. */
+ * rounds, 0 = all): the n < 1024 circuits in one cooperative persistent
+ * kernel launch on the batch's stream, the others on the worker streams.
+ * Returns when all work is enqueued (the host threads wait for their streams
+ * once per block of measurements); the batch's stream then waits for the
+ * worker streams, so work enqueued on it afterwards follows the whole batch.
+ * tuning: NULL for the default shape of the persistent kernel. */
 int qs_batch_run(qs_batch *batch, const qs_batch_tuning *tuning, uint32_t round_limit);
 
 /* Waits for the batch's stream; QS_ERR_TIMEOUT if a grid barrier ran out,
@@ -367,8 +380,9 @@ int qs_batch_record(qs_batch *batch, uint32_t circuit, uint8_t *dst, size_t coun
 int qs_batch_export_rows(qs_batch *batch, uint32_t circuit, const uint32_t *rows, uint32_t count,
                          uint64_t *dst);
 
-/* Times the candidate launch shapes on this batch (the first round_limit
- * rounds; 0 = all) and returns the fastest. cache_path: NULL, or a text file
+/* Times the candidate launch shapes of the persistent kernel on this batch
+ * (the first round_limit rounds; 0 = all; the worker streams are idle
+ * meanwhile) and returns the fastest. cache_path: NULL, or a text file
  * of "device|batch-signature|rounds threads blocks_per_sm words_per_block
  * fuse_depth" lines that is read first and appended to. Results do not depend
  * on the shape. */

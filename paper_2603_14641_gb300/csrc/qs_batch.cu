@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
+#include <thread>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -40,6 +42,13 @@ namespace qs {
 
 constexpr int64_t kBNoPivot = LLONG_MAX;
 constexpr uint32_t kBatchMaxQubits = 8192;  // det partials: <= 4 words per lane
+// Circuits of at least this many qubits run through per-circuit simulators
+// (blocked measurement, 64 measurements per tableau pass) on worker streams;
+// the persistent kernel takes the smaller ones, whose per-launch costs
+// dominate when they run alone.
+constexpr uint32_t kBatchSimMinQubits = 1024;
+constexpr uint32_t kBatchMaxWorkers = 16;
+constexpr uint32_t kBatchLimitQubits = 1u << 20;
 
 struct BCirc {
   uint32_t n, k, cs, rs, ncols, nrows;
@@ -540,6 +549,16 @@ struct Carve2 {
 
 }  // namespace
 
+// A large circuit of the batch, simulated by its own qs_sim on a worker stream.
+struct BSim {
+  uint32_t index = 0;
+  qs_sim *sim = nullptr;
+  uint32_t *packed_dev = nullptr;  // qs_pack_layers records, device
+  std::vector<int64_t> lp;         // layer offsets
+  std::vector<uint32_t> rl, rm, qubits;
+  uint64_t seed = 0, shot = 0;
+};
+
 struct qs_batch {
   cudaStream_t stream = nullptr;
   void *ws = nullptr;
@@ -559,7 +578,28 @@ struct qs_batch {
   uint32_t built_wpb = 0;
   uint64_t signature = 0;
   int sms = 152;
+  bool any_small = false;               // the persistent kernel has work
+  std::vector<int32_t> sim_of;          // per circuit: index into sims, or -1
+  std::vector<BSim> sims;
+  std::vector<cudaStream_t> wstreams;   // worker streams of the large circuits
+  std::vector<cudaEvent_t> wevents;
+  cudaEvent_t start_ev = nullptr;       // worker streams start after the batch stream's earlier work
+  bool skip_sims = false;               // set while autotuning the persistent kernel
 };
+
+static void free_sims(qs_batch *b) {
+  for (BSim &x : b->sims) {
+    if (x.sim) qs_sim_destroy(x.sim);
+    if (x.packed_dev) cudaFree(x.packed_dev);
+  }
+  b->sims.clear();
+  for (cudaEvent_t e : b->wevents) cudaEventDestroy(e);
+  for (cudaStream_t st : b->wstreams) cudaStreamDestroy(st);
+  if (b->start_ev) cudaEventDestroy(b->start_ev);
+  b->start_ev = nullptr;
+  b->wevents.clear();
+  b->wstreams.clear();
+}
 
 static void layout_of(uint32_t n, uint32_t &k, uint32_t &cs, uint32_t &ncols, uint32_t &rs,
                       uint32_t &nrows) {
@@ -626,8 +666,8 @@ static int validate_batch(uint32_t count, const qs_batch_circuit *cc) {
   char buf[200];
   for (uint32_t i = 0; i < count; ++i) {
     const qs_batch_circuit &c = cc[i];
-    if (c.n == 0 || c.n > kBatchMaxQubits) {
-      snprintf(buf, sizeof buf, "circuit %u: n must be in [1, %u]", i, kBatchMaxQubits);
+    if (c.n == 0 || c.n > kBatchLimitQubits) {
+      snprintf(buf, sizeof buf, "circuit %u: n must be in [1, %u]", i, kBatchLimitQubits);
       return bfail(QS_ERR_ARG, buf);
     }
     if (c.n_layers && (!c.layer_ptr || (!c.gates && c.layer_ptr[c.n_layers] > 0)))
@@ -718,15 +758,31 @@ static int build_acts(qs_batch *b, uint32_t wpb) {
   return QS_OK;
 }
 
+// The persistent kernel's view of the batch: large circuits become empty
+// one-qubit programs (their work runs through per-circuit simulators).
+static std::vector<qs_batch_circuit> kernel_view(uint32_t count, const qs_batch_circuit *cc) {
+  std::vector<qs_batch_circuit> v(cc, cc + count);
+  for (qs_batch_circuit &c : v)
+    if (c.n >= kBatchSimMinQubits) {
+      const uint64_t seed = c.seed, shot = c.shot;
+      c = qs_batch_circuit{};
+      c.n = 1;
+      c.seed = seed;
+      c.shot = shot;
+    }
+  return v;
+}
+
 extern "C" {
 
 const char *qs_batch_last_error(void) { return g_batch_err.c_str(); }
 
 size_t qs_batch_required_bytes(uint32_t count, const qs_batch_circuit *circuits) {
   if (validate_batch(count, circuits)) return 0;
+  const std::vector<qs_batch_circuit> kv = kernel_view(count, circuits);
   BatchPlan P;
   uint32_t nr;
-  plan_batch(count, circuits, P, nr);
+  plan_batch(count, kv.data(), P, nr);
   return P.total;
 }
 
@@ -736,6 +792,9 @@ int qs_batch_create(uint32_t count, const qs_batch_circuit *cc, void *stream, vo
   *out = nullptr;
   int rc = validate_batch(count, cc);
   if (rc) return rc;
+  const qs_batch_circuit *orig = cc;
+  const std::vector<qs_batch_circuit> kv = kernel_view(count, cc);
+  cc = kv.data();
   if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255))
     return bfail(QS_ERR_ARG, "workspace must be 256-byte aligned");
   BatchPlan P;
@@ -814,6 +873,7 @@ int qs_batch_create(uint32_t count, const qs_batch_circuit *cc, void *stream, vo
     b->rm[i].assign(c.round_meas ? c.round_meas : nullptr,
                     c.round_meas ? c.round_meas + c.n_rounds + 1 : nullptr);
     if (b->rl[i].empty()) { b->rl[i].push_back(0); b->rm[i].push_back(0); }
+    if (orig[i].n < kBatchSimMinQubits && (G > 0 || M > 0)) b->any_small = true;
     pre_n[i + 1] = pre_n[i] + c.n;
     b->n_max = std::max(b->n_max, c.n);
     mix(c.n); mix(c.n_rounds); mix((uint64_t)G); mix(M);
@@ -841,6 +901,73 @@ int qs_batch_create(uint32_t count, const qs_batch_circuit *cc, void *stream, vo
     delete b;
     return bfail(QS_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
   }
+  // large circuits: one simulator each, spread over the worker streams by size
+  b->sim_of.assign(count, -1);
+  std::vector<uint32_t> large;
+  for (uint32_t i = 0; i < count; ++i)
+    if (orig[i].n >= kBatchSimMinQubits) large.push_back(i);
+  std::stable_sort(large.begin(), large.end(),
+                   [&](uint32_t x, uint32_t y) { return orig[x].n > orig[y].n; });
+  const uint32_t nw = std::min<uint32_t>(kBatchMaxWorkers, (uint32_t)large.size());
+  if (nw && cudaEventCreateWithFlags(&b->start_ev, cudaEventDisableTiming) != cudaSuccess)
+    rc = bfail(QS_ERR_CUDA, "batch event creation failed");
+  for (uint32_t w = 0; w < nw && rc == QS_OK; ++w) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      if (st) cudaStreamDestroy(st);
+      rc = bfail(QS_ERR_CUDA, "worker stream creation failed");
+      break;
+    }
+    b->wstreams.push_back(st);
+    b->wevents.push_back(ev);
+  }
+  for (size_t j = 0; j < large.size() && rc == QS_OK; ++j) {
+    const uint32_t i = large[j];
+    const qs_batch_circuit &c = orig[i];
+    BSim x;
+    x.index = i;
+    x.seed = c.seed;
+    x.shot = c.shot;
+    const uint64_t M = c.n_rounds ? c.round_meas[c.n_rounds] : 0;
+    b->meas_total[i] = M;
+    x.rl.assign(c.round_layers ? c.round_layers : nullptr,
+                c.round_layers ? c.round_layers + c.n_rounds + 1 : nullptr);
+    x.rm.assign(c.round_meas ? c.round_meas : nullptr,
+                c.round_meas ? c.round_meas + c.n_rounds + 1 : nullptr);
+    if (M) x.qubits.assign(c.qubits, c.qubits + M);
+    const int64_t G = c.n_layers ? c.layer_ptr[c.n_layers] : 0;
+    x.lp.assign(c.layer_ptr ? c.layer_ptr : nullptr, c.layer_ptr ? c.layer_ptr + c.n_layers + 1 : nullptr);
+    if (x.lp.empty()) x.lp.push_back(0);
+    std::vector<uint32_t> packed(2 * (size_t)std::max<int64_t>(G, 1), 0);
+    if (c.n_layers && (rc = qs_pack_layers(c.n, c.gates, c.layer_ptr, c.n_layers, packed.data()))) {
+      rc = bfail(rc, std::string("circuit ") + std::to_string(i) + ": " + qs_last_error());
+      break;
+    }
+    if (cudaMalloc(&x.packed_dev, packed.size() * 4) != cudaSuccess ||
+        cudaMemcpy(x.packed_dev, packed.data(), packed.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      if (x.packed_dev) cudaFree(x.packed_dev);
+      rc = bfail(QS_ERR_OOM, "gate records of a large circuit");
+      break;
+    }
+    qs_options opt{};
+    opt.record_capacity = std::max<uint64_t>(M, 1);
+    if ((rc = qs_sim_create(c.n, &opt, b->wstreams[j % nw], nullptr, 0, &x.sim))) {
+      cudaFree(x.packed_dev);
+      rc = bfail(rc, std::string("circuit ") + std::to_string(i) + ": " + qs_last_error());
+      break;
+    }
+    b->sim_of[i] = (int32_t)b->sims.size();
+    b->sims.push_back(std::move(x));
+  }
+  if (rc != QS_OK) {
+    free_sims(b);
+    if (b->owns) cudaFree(b->ws);
+    delete b;
+    return rc;
+  }
   *out = b;
   return QS_OK;
 }
@@ -848,6 +975,7 @@ int qs_batch_create(uint32_t count, const qs_batch_circuit *cc, void *stream, vo
 int qs_batch_destroy(qs_batch *b) {
   if (!b) return QS_OK;
   cudaStreamSynchronize(b->stream);
+  free_sims(b);
   if (b->owns && b->ws) cudaFree(b->ws);
   delete b;
   return QS_OK;
@@ -865,9 +993,77 @@ static int tuning_ok(const qs_batch *b, const qs_batch_tuning &t, size_t *smem) 
   return QS_OK;
 }
 
+static int run_kernel(qs_batch *b, const qs_batch_tuning *tuning, uint32_t round_limit);
+
+// Enqueues every large circuit's rounds on its simulator, one host thread per
+// worker stream (blocked measurement waits for its stream once per block),
+// then makes the batch stream wait for the worker streams.
+static int run_sims(qs_batch *b, uint32_t round_limit) {
+  const uint32_t nw = (uint32_t)b->wstreams.size();
+  std::mutex mu;
+  int first_rc = QS_OK;
+  std::string first_msg;
+  auto worker = [&](uint32_t w) {
+    int rc = QS_OK;
+    if (cudaStreamWaitEvent(b->wstreams[w], b->start_ev, 0) != cudaSuccess) rc = QS_ERR_CUDA;
+    for (size_t j = w; j < b->sims.size() && rc == QS_OK; j += nw) {
+      BSim &x = b->sims[j];
+      rc = qs_sim_reset(x.sim, nullptr);
+      const uint32_t nr = x.rl.empty() ? 0 : (uint32_t)x.rl.size() - 1;
+      const uint32_t lim = std::min(nr, round_limit);
+      for (uint32_t r = 0; r < lim && rc == QS_OK; ++r) {
+        if (x.rl[r + 1] > x.rl[r])
+          rc = qs_sim_apply_layers_dev(x.sim, x.packed_dev, x.lp.data(), x.rl[r], x.rl[r + 1]);
+        if (rc == QS_OK && x.rm[r + 1] > x.rm[r])
+          rc = qs_sim_measure(x.sim, x.qubits.data() + x.rm[r], x.rm[r + 1] - x.rm[r],
+                              qs_key{x.seed, x.shot}, nullptr);
+      }
+      if (rc != QS_OK) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (first_rc == QS_OK) {
+          first_rc = rc;
+          first_msg = std::string("circuit ") + std::to_string(x.index) + ": " + qs_last_error();
+        }
+      }
+    }
+    if (cudaEventRecord(b->wevents[w], b->wstreams[w]) != cudaSuccess) {
+      std::lock_guard<std::mutex> lock(mu);
+      if (first_rc == QS_OK) { first_rc = QS_ERR_CUDA; first_msg = "worker event record failed"; }
+    }
+  };
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<std::thread> threads;
+  for (uint32_t w = 0; w < nw; ++w)
+    threads.emplace_back([&, w]() {
+      cudaSetDevice(dev);
+      worker(w);
+    });
+  for (std::thread &t : threads) t.join();
+  for (uint32_t w = 0; w < nw && first_rc == QS_OK; ++w)
+    if (cudaStreamWaitEvent(b->stream, b->wevents[w], 0) != cudaSuccess) {
+      first_rc = QS_ERR_CUDA;
+      first_msg = "batch stream wait failed";
+    }
+  if (first_rc != QS_OK) return bfail(first_rc, first_msg);
+  return QS_OK;
+}
+
 int qs_batch_run(qs_batch *b, const qs_batch_tuning *tuning, uint32_t round_limit) {
   if (!b) return bfail(QS_ERR_ARG, "batch is NULL");
   if (b->broken) return bfail(QS_ERR_STATE, "batch is unusable after an earlier device error");
+  int rc = QS_OK;
+  const bool sims = !b->skip_sims && !b->sims.empty();
+  if (sims && cudaEventRecord(b->start_ev, b->stream) != cudaSuccess)
+    return bfail(QS_ERR_CUDA, "batch event record failed");
+  if (b->any_small || b->sims.empty()) {
+    if ((rc = run_kernel(b, tuning, round_limit))) return rc;
+  }
+  if (sims) rc = run_sims(b, round_limit ? round_limit : 0xFFFFFFFFu);
+  return rc;
+}
+
+static int run_kernel(qs_batch *b, const qs_batch_tuning *tuning, uint32_t round_limit) {
   qs_batch_tuning t = tuning ? *tuning : qs_batch_tuning{512, 0, 1, 0, 0};
   if (t.spin_limit == 0) t.spin_limit = 20ull * 1000 * 1000;  // x >=128 ns: several seconds
   size_t smem = 0;
@@ -929,6 +1125,10 @@ int qs_batch_sync(qs_batch *b) {
     snprintf(buf, sizeof buf, "batch self-check failed (flags 0x%x)", flags);
     return bfail(QS_ERR_INTERNAL, buf);
   }
+  for (BSim &x : b->sims) {
+    const int rc = qs_sim_sync(x.sim);
+    if (rc) return bfail(rc, std::string("circuit ") + std::to_string(x.index) + ": " + qs_last_error());
+  }
   return QS_OK;
 }
 
@@ -937,6 +1137,10 @@ int qs_batch_record(qs_batch *b, uint32_t circuit, uint8_t *dst, size_t count) {
   if (count > b->meas_total[circuit]) return bfail(QS_ERR_ARG, "count beyond the circuit's record");
   int rc = qs_batch_sync(b);
   if (rc) return rc;
+  if (b->sim_of[circuit] >= 0) {
+    rc = count ? qs_sim_record(b->sims[b->sim_of[circuit]].sim, 0, count, dst) : QS_OK;
+    return rc ? bfail(rc, qs_last_error()) : QS_OK;
+  }
   if (count && cudaMemcpy(dst, b->circs[circuit].record, count, cudaMemcpyDeviceToHost) != cudaSuccess)
     return bfail(QS_ERR_CUDA, "record copy failed");
   return QS_OK;
@@ -947,6 +1151,10 @@ int qs_batch_export_rows(qs_batch *b, uint32_t circuit, const uint32_t *rows, ui
   if (!b || circuit >= b->count) return bfail(QS_ERR_ARG, "bad batch or circuit index");
   int rc = qs_batch_sync(b);
   if (rc) return rc;
+  if (b->sim_of[circuit] >= 0) {
+    rc = qs_sim_export_rows(b->sims[b->sim_of[circuit]].sim, rows, count, dst);
+    return rc ? bfail(rc, qs_last_error()) : QS_OK;
+  }
   const BCirc &C = b->circs[circuit];
   for (uint32_t i = 0; i < count; ++i)
     if (rows[i] >= 2 * C.n) return bfail(QS_ERR_ARG, "row index >= 2n");
@@ -1009,6 +1217,11 @@ int qs_batch_autotune(qs_batch *b, uint32_t round_limit, const char *cache_path,
       }
     }
   }
+  if (!b->any_small) {  // every circuit runs through a simulator: nothing to tune
+    *best = qs_batch_tuning{512, 0, 1, 0, 0};
+    return QS_OK;
+  }
+  b->skip_sims = true;  // time the persistent kernel alone
   const uint32_t threads[] = {256, 512, 1024};
   const uint32_t bps[] = {1, 2, 4};
   const uint32_t wpbs[] = {1, 2};
@@ -1040,6 +1253,7 @@ int qs_batch_autotune(qs_batch *b, uint32_t round_limit, const char *cache_path,
         }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  b->skip_sims = false;
   g_batch_err.clear();
   *best = best_t;
   if (cache_path && best_ms < 1e29f) {

@@ -602,7 +602,7 @@ size_t blocked_scratch_bytes(const Layout &L) {
          2 * al(64ull * L.rs * 8) + al(sizeof(BlkState));
 }
 
-static uint64_t g_apply_attr_set = 0;
+static std::atomic<uint64_t> g_apply_attr_set{0};
 
 // Enqueues one block of up to 64 measurements; the number actually done is
 // st->len (read by the host after the stream is synchronised).
@@ -623,9 +623,7 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   BlkState *st = reinterpret_cast<BlkState *>(take(sizeof(BlkState)));
   const unsigned rb = (unsigned)((L.nrows + 255) / 256);
   const size_t smem = (size_t)kEntries * kEntryBytes;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !((g_apply_attr_set >> dev) & 1u)) {
+  cudaError_t ea = once_per_device(g_apply_attr_set, [&]() {
     cudaError_t e = cudaFuncSetAttribute(blk_apply_kernel<uint32_t>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
@@ -637,9 +635,9 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(blk_symbolic_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(kSymSmallRows * sizeof(uint64_t)));
-    if (e != cudaSuccess) return e;
-    g_apply_attr_set |= 1ull << dev;
-  }
+    return e;
+  });
+  if (ea != cudaSuccess) return ea;
   blk_reset_kernel<<<1, 64, 0, s>>>(st, B);
   blk_init_kernel<<<rb, 256, 0, s>>>(d.RX, L.rs, L.nrows, L.n, L.k, qubits, B, C0, M, base, st,
                                      d.err);

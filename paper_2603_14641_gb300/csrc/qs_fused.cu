@@ -109,16 +109,12 @@ template <bool SIGNS, int WPB>
 static cudaError_t launch_fused_t(uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t n, uint32_t stride,
                                   uint32_t nwords, const uint32_t *packed, const int64_t *lptr,
                                   uint32_t L, uint32_t *err, cudaStream_t s) {
-  static uint64_t attr_set = 0;  // one bit per device ordinal
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !((attr_set >> dev) & 1u)) {
-    cudaError_t e = cudaFuncSetAttribute(fused_segment_kernel<SIGNS, WPB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kFusedSmemMax);
-    if (e != cudaSuccess) return e;
-    attr_set |= 1ull << dev;
-  }
+  static std::atomic<uint64_t> attr_set{0};  // one bit per device ordinal
+  cudaError_t ea = once_per_device(attr_set, []() {
+    return cudaFuncSetAttribute(fused_segment_kernel<SIGNS, WPB>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemMax);
+  });
+  if (ea != cudaSuccess) return ea;
   const size_t smem = (size_t)16 * n * WPB;
   const uint32_t blocks = (nwords + WPB - 1) / WPB;
   uint32_t threads = 1024;

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include <string>
 #include <vector>
 
@@ -83,6 +85,22 @@ __device__ __forceinline__ P4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c
 constexpr uint64_t kCoinKey = 0x51A7Eull;
 constexpr uint64_t kFrameKey = 0xF4A3Eull;
 constexpr uint64_t kNoiseKey = 0xE5505ull;
+
+// Runs `set` (kernel attribute calls) once per device ordinal, safely from
+// several host threads: `done` holds one bit per device already set (ordinals
+// >= 64 set every time). Setting an attribute twice is harmless.
+template <class F>
+inline cudaError_t once_per_device(std::atomic<uint64_t> &done, F set) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64) return set();
+  const uint64_t bit = 1ull << dev;
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // ------------------------------------------------------------------------
 // Launchers (each returns cudaGetLastError() after the launch).

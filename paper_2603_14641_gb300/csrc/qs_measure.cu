@@ -276,7 +276,7 @@ finalize_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t r
   if (threadIdx.x == 0) { mst[kMsPivot] = kNoPivot; mst[kMsDetCross] = 0; }
 }
 
-static bool g_rowsum_attr_set = false;
+static std::atomic<uint64_t> g_rowsum_attr_set{0};
 
 cudaError_t launch_measure_one(const Dev &d, const uint32_t *qubits, uint32_t i, uint64_t midx,
                                qs_key key, cudaStream_t s, int *launches) {
@@ -285,9 +285,12 @@ cudaError_t launch_measure_one(const Dev &d, const uint32_t *qubits, uint32_t i,
   gather_kernel<<<gblocks, 256, 0, s>>>(d.RX, L.rs, L.nrows, L.n, L.k, qubits, i, d.colx, d.mst,
                                         d.err);
   const size_t smem = 2ull * L.rs * sizeof(uint64_t);
-  if (smem > 48 * 1024 && !g_rowsum_attr_set) {
-    cudaFuncSetAttribute(rowsum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    g_rowsum_attr_set = true;
+  if (smem > 48 * 1024) {
+    cudaError_t ea = once_per_device(g_rowsum_attr_set, []() {
+      return cudaFuncSetAttribute(rowsum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  227 * 1024);
+    });
+    if (ea != cudaSuccess) return ea;
   }
   const int sms = d.sms;
   // rows per warp ~ nrows / warps; at most 4 blocks of 512 per SM
@@ -548,7 +551,7 @@ meas_finalize_gather_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ
   }
 }
 
-static uint64_t g_update_attr_set = 0;
+static std::atomic<uint64_t> g_update_attr_set{0};
 
 template <int UPT>
 static void launch_update_t(const Dev &d, uint32_t rblocks, size_t smem, const uint32_t *qubits,
@@ -566,17 +569,16 @@ cudaError_t launch_measure_window(const Dev &d, const uint32_t *qubits, uint32_t
   if (count == 0) return cudaSuccess;
   const Layout &L = d.L;
   const size_t smem = 2ull * L.rs * sizeof(uint64_t);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !((g_update_attr_set >> dev) & 1u)) {
+  cudaError_t ea = once_per_device(g_update_attr_set, []() {
     for (cudaError_t e : {cudaFuncSetAttribute(meas_update_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
                           cudaFuncSetAttribute(meas_update_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
                           cudaFuncSetAttribute(meas_update_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
                           cudaFuncSetAttribute(meas_update_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
                           cudaFuncSetAttribute(meas_update_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)})
       if (e != cudaSuccess) return e;
-    g_update_attr_set |= 1ull << dev;
-  }
+    return cudaSuccess;
+  });
+  if (ea != cudaSuccess) return ea;
   const uint64_t want = (L.nrows + 15) / 16;
   const uint32_t rblocks = (uint32_t)std::min<uint64_t>((uint64_t)d.sms * 4, std::max<uint64_t>(1, want));
   const uint32_t nchunks = std::min<uint32_t>(std::min<uint32_t>(kDetBlocks, L.k), rblocks);

@@ -116,6 +116,28 @@ def test_batch_rejects_bad_programs():
     with pytest.raises(qs.QsError) as e:
         qs.Batch([c, bad], [1, 2], device="cuda:0")
     assert e.value.code == -1
-    big = C.random_circuit(9000, 1, 0.5, seed=1)
+    empty = C.Circuit(n=0, gates=np.zeros((0, 3), np.uint32), layer_ptr=np.array([0]), ops=[])
     with pytest.raises(qs.QsError):
-        qs.Batch([big], [1], device="cuda:0")
+        qs.Batch([c, empty], [1, 2], device="cuda:0")
+
+
+def test_batch_large_circuits_run_through_simulators():
+    """n >= 1024 circuits (here up to 9,000 qubits, beyond the persistent
+    kernel's shared-memory limit) mixed with small ones: every record and
+    sampled rows equal the single-circuit path, over repeated runs and a
+    round limit."""
+    circs = [C.random_circuit(n, 20, 0.5, seed=n, measure_every=5, measure_frac=0.1)
+             for n in (9000, 300, 1024, 50, 2048, 1500)]
+    seeds = [11 * i + 3 for i in range(len(circs))]
+    b = qs.Batch(circs, seeds, device="cuda:0")
+    for _ in range(2):
+        b.run()
+        b.sync()
+    for i, c in enumerate(circs):
+        s = qs.Simulator(c.n, device="cuda:0")
+        rec = s.run(c, seed=seeds[i])
+        assert np.array_equal(b.record(i), rec), f"circuit {i} (n={c.n})"
+        rows = np.arange(0, 2 * c.n, max(1, (2 * c.n) // 30), dtype=np.uint32)
+        bx, bz, br = b.export_rows(i, rows)
+        sx, sz, sr = s.export_rows(rows)
+        assert np.array_equal(bx, sx) and np.array_equal(bz, sz) and np.array_equal(br, sr)
