@@ -8,7 +8,8 @@
 // bit matrix M stored as `in` rows of words (bit b of in[i][j] = M[i][64 j + b])
 // and writes M^T the same way.
 //
-// A block is four warps and covers 256 input rows x 4 input words:
+// Small matrices: a block is four warps and covers 256 input rows x 4 input
+// words:
 //   - lane l of warp w loads input rows 64 w + l and 64 w + l + 32, 4 words
 //     each (one full 32-byte sector per row);
 //   - each 64 x 64 bit sub-tile is transposed in registers in six
@@ -87,22 +88,93 @@ bit_transpose_kernel(const uint64_t *__restrict__ in, size_t in_stride, uint64_t
   }
 }
 
+// Large matrices: a block of 512 threads covers 512 input rows x 16 input
+// words, so reads are 128-byte row segments and writes 64-byte ones (32-byte
+// segments reach only about a third of the HBM bandwidth). The tile is staged
+// in shared memory (70 KB, three blocks per SM overlap their load, transpose
+// and store phases), each warp transposes 64 x 64 sub-tiles in registers and
+// writes them back in place, and 1024 output rows of 8 words leave the
+// block. Row stride 17 words and an XOR swizzle of the word index by the
+// 64-row group keep the three shared-memory passes free of bank conflicts.
+// Partial tiles at the matrix edge read zeros and write only in-range words.
+constexpr int kTR = 512, kTW = 16, kTP = 17, kTT = 512;  // rows, words, row stride, threads
+constexpr size_t kBigTileSmem = (size_t)kTR * kTP * sizeof(uint64_t);
+
+__device__ __forceinline__ int tsw(int row, int w) { return row * kTP + (w ^ (row >> 6)); }
+
+__global__ void __launch_bounds__(kTT, 3)
+bit_transpose_big_kernel(const uint64_t *__restrict__ in, size_t in_stride, size_t rows_in,
+                         size_t words_in, uint64_t *__restrict__ out, size_t out_stride) {
+  extern __shared__ uint64_t tl[];  // [kTR][kTP], word index swizzled
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const size_t i0 = (size_t)blockIdx.y * kTR, j0 = (size_t)blockIdx.x * kTW;
+  const int vr = (int)min((size_t)kTR, rows_in - i0), vw = (int)min((size_t)kTW, words_in - j0);
+  // 1: 16 words of a row per half warp (128-byte segments)
+#pragma unroll 4
+  for (int it = 0; it < kTR * kTW / kTT; ++it) {
+    const int idx = it * kTT + t, row = idx / kTW, w = idx % kTW;
+    uint64_t v = 0;
+    if (row < vr && w < vw) v = in[(i0 + row) * in_stride + j0 + w];
+    tl[tsw(row, w)] = v;
+  }
+  __syncthreads();
+  // 2: 256 sub-tiles (16 row groups x 16 words), 8 per warp
+#pragma unroll 1
+  for (int k = 0; k < (kTR / 64) * kTW / (kTT / 32); ++k) {
+    const int st = warp * ((kTR / 64) * kTW / (kTT / 32)) + k, rt = st / kTW, w = st % kTW;
+    uint64_t lo = tl[tsw(64 * rt + lane, w)], hi = tl[tsw(64 * rt + lane + 32, w)];
+    transpose64(lo, hi, lane);
+    // now lo = output row 64 w + lane, word rt; hi = output row 64 w + lane + 32
+    tl[tsw(64 * rt + lane, w)] = lo;
+    tl[tsw(64 * rt + lane + 32, w)] = hi;
+  }
+  __syncthreads();
+  // 3: output row 64 w + b, word rt sits at [64 rt + b][w]; kTR / 64 words per output row
+  const int vrt = vr / 64;  // rows_in is a multiple of 64
+#pragma unroll 4
+  for (int it = 0; it < kTR * kTW / kTT; ++it) {
+    const int idx = it * kTT + t, orl = idx / (kTR / 64), rt = idx % (kTR / 64);
+    const int w = orl / 64, b = orl % 64;
+    if (w < vw && rt < vrt)
+      out[(64 * (j0 + w) + b) * out_stride + i0 / 64 + rt] = tl[tsw(64 * rt + b, w)];
+  }
+}
+
+static std::atomic<uint64_t> g_big_tile_attr{0};
+
+static cudaError_t transpose(const uint64_t *in, size_t in_stride, size_t rows_in, size_t words_in,
+                             uint64_t *out, size_t out_stride, cudaStream_t s) {
+  if (rows_in >= (size_t)kTR && words_in >= (size_t)kTW) {
+    cudaError_t e = once_per_device(g_big_tile_attr, []() {
+      return cudaFuncSetAttribute(bit_transpose_big_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBigTileSmem);
+    });
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((words_in + kTW - 1) / kTW), (unsigned)((rows_in + kTR - 1) / kTR));
+    bit_transpose_big_kernel<<<grid, kTT, kBigTileSmem, s>>>(in, in_stride, rows_in, words_in, out,
+                                                               out_stride);
+  } else {
+    // rows_in is a multiple of 256 and words_in of 4 by construction
+    dim3 grid((unsigned)(words_in / 4), (unsigned)(rows_in / 256));
+    bit_transpose_kernel<<<grid, 128, 0, s>>>(in, in_stride, out, out_stride);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_to_rows(const Dev &d, cudaStream_t s) {
   // in = X/Z: rows = ncols (qubits), words = cs; out = RX/RZ: rows = 64 cs, words = rs
   const Layout &L = d.L;
-  dim3 grid(L.cs / 4, L.ncols / 256);
-  bit_transpose_kernel<<<grid, 128, 0, s>>>(d.X, L.cs, d.RX, L.rs);
-  bit_transpose_kernel<<<grid, 128, 0, s>>>(d.Z, L.cs, d.RZ, L.rs);
-  return cudaGetLastError();
+  cudaError_t e = transpose(d.X, L.cs, L.ncols, L.cs, d.RX, L.rs, s);
+  if (e == cudaSuccess) e = transpose(d.Z, L.cs, L.ncols, L.cs, d.RZ, L.rs, s);
+  return e;
 }
 
 cudaError_t launch_to_cols(const Dev &d, cudaStream_t s) {
   // in = RX/RZ: rows = 64 cs, words = rs; out = X/Z: rows = 64 rs = ncols, words = cs
   const Layout &L = d.L;
-  dim3 grid(L.rs / 4, (unsigned)(L.nrows / 256));
-  bit_transpose_kernel<<<grid, 128, 0, s>>>(d.RX, L.rs, d.X, L.cs);
-  bit_transpose_kernel<<<grid, 128, 0, s>>>(d.RZ, L.rs, d.Z, L.cs);
-  return cudaGetLastError();
+  cudaError_t e = transpose(d.RX, L.rs, L.nrows, L.rs, d.X, L.cs, s);
+  if (e == cudaSuccess) e = transpose(d.RZ, L.rs, L.nrows, L.rs, d.Z, L.cs, s);
+  return e;
 }
 
 }  // namespace qs
