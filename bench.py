@@ -709,10 +709,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rows", type=int, default=64)
-    ap.add_argument("--cpu-layers", type=int, default=20)
-    ap.add_argument("--cpu-meas-n", type=int, default=2_000)
-    ap.add_argument("--cpu-meas-count", type=int, default=50)
+    ap.add_argument("--cpu-rows", type=int, default=256)
+    ap.add_argument("--cpu-layers", type=int, default=40)
+    ap.add_argument("--cpu-meas-n", type=int, default=3_000)
+    ap.add_argument("--cpu-meas-count", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
