@@ -239,8 +239,10 @@ blk_replay_kernel(uint64_t nrows, uint32_t k, const uint64_t *__restrict__ C0,
 // V_j is the product of the original pivot rows p_s over a set E_j of steps:
 // E_j = {j} xor (xor of E_s over the steps s that targeted p_j before step j),
 // built by one warp in step order; every V_j of the chunk is then independent.
-// Lane = column word; warp w takes steps w, w + 16, ...
-constexpr int kVrowThreads = 512;
+// Lane = column word; warp w takes steps w, w + 32; four blocks per chunk
+// share the pairwise parities G.
+constexpr int kVrowThreads = 1024;
+constexpr int kVrowSplit = 4;  // blocks per chunk; block y computes G rows 16 y .. 16 y + 15
 constexpr size_t kVrowSmem = 4ull * 64 * 32 * sizeof(uint64_t);  // original and V rows, x and z
 
 __global__ void __launch_bounds__(kVrowThreads)
@@ -254,6 +256,7 @@ blk_vrows_kernel(const uint64_t *__restrict__ RX, const uint64_t *__restrict__ R
   __shared__ uint64_t sE[64];
   const int L = st->len;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool lead = blockIdx.y == 0;  // writes the V rows and the per-step sums
   // every word of the padded row (u < rs): padding qubit words are zero in the
   // tableau and come out zero in the V rows too
   const uint32_t u = blockIdx.x * 32 + lane;
@@ -275,17 +278,20 @@ blk_vrows_kernel(const uint64_t *__restrict__ RX, const uint64_t *__restrict__ R
     }
   }
   __syncthreads();
+  // every block builds all V rows of its chunk (G needs them); the lead block
+  // also stores them and adds the per-step popcount sums
   for (int j = w; j < L; j += nw) {
     const uint64_t x0 = ox[j][lane], z0 = oz[j][lane];
     uint64_t ax = x0, az = z0, e = sE[j] & ~(1ull << j);
     while (e) {
-      const int s = __ffsll((long long)e) - 1;
+      const int s2 = __ffsll((long long)e) - 1;
       e &= e - 1;
-      ax ^= ox[s][lane];
-      az ^= oz[s][lane];
+      ax ^= ox[s2][lane];
+      az ^= oz[s2][lane];
     }
     vx[j][lane] = ax;
     vz[j][lane] = az;
+    if (!lead) continue;
     if (in) {
       VX[(uint64_t)j * rs + u] = ax;
       VZ[(uint64_t)j * rs + u] = az;
@@ -303,15 +309,17 @@ blk_vrows_kernel(const uint64_t *__restrict__ RX, const uint64_t *__restrict__ R
     }
   }
   __syncthreads();
-  // G[s] bit t = parity of z_{V_s} . x_{V_t} over the chunk
-  for (int s = w; s < L; s += nw) {
-    const uint64_t zs = vz[s][lane];
+  // G[s] bit t = parity of z_{V_s} . x_{V_t} over the chunk: block y takes
+  // s = 16 y + w / 2, each warp half of the t range
+  const int sg = 16 * (int)blockIdx.y + (w >> 1), t0 = 32 * (w & 1);
+  if (sg < L) {
+    const uint64_t zs = vz[sg][lane];
     uint64_t row = 0;
-    for (int t = 0; t < L; ++t) {
+    for (int t = t0; t < t0 + 32 && t < L; ++t) {
       const uint32_t bal = __ballot_sync(0xffffffffu, __popcll(zs & vx[t][lane]) & 1);
       row |= (uint64_t)(__popc(bal) & 1) << t;
     }
-    if (lane == 0 && row) atomicXor(reinterpret_cast<unsigned long long *>(&st->G[s]), row);
+    if (lane == 0 && row) atomicXor(reinterpret_cast<unsigned long long *>(&st->G[sg]), row);
   }
 }
 
@@ -334,19 +342,26 @@ __device__ __forceinline__ int cross_pairs(const uint64_t *G, uint64_t m) {
 // step order: rV_j = (e'_j >> 1) ^ parity(m_j & {s : rV_s = 1}).
 __global__ void __launch_bounds__(64) blk_signs_kernel(const uint64_t *__restrict__ S, BlkState *st,
                                                        uint32_t *err) {
-  __shared__ int sb[64];
+  __shared__ int sb[64], sA[64];
+  __shared__ uint64_t sm[64], sG[64];
   const int L = st->len, j = threadIdx.x;
   if (j < L) {
+    sm[j] = st->mpiv[j];
+    sA[j] = st->A[j];
+    sG[j] = st->G[j];
+  }
+  __syncthreads();
+  if (j < L) {
     const int64_t p = st->piv[j];
-    const uint64_t m = st->mpiv[j];
-    int e = 2 * (int)((S[p >> 6] >> (p & 63)) & 1u) + st->B0[j] - st->A[j] + 2 * st->Cp[j];
+    const uint64_t m = sm[j];
+    int e = 2 * (int)((S[p >> 6] >> (p & 63)) & 1u) + st->B0[j] - sA[j] + 2 * st->Cp[j];
     uint64_t mm = m;
     while (mm) {
       const int s = __ffsll((long long)mm) - 1;
       mm &= mm - 1;
-      e += st->A[s];
+      e += sA[s];
     }
-    e += 2 * cross_pairs(st->G, m);
+    e += 2 * cross_pairs(sG, m);
     sb[j] = m4(e);
   }
   __syncthreads();
@@ -355,10 +370,10 @@ __global__ void __launch_bounds__(64) blk_signs_kernel(const uint64_t *__restric
     for (int i = 0; i < L; ++i) {
       const int e = sb[i];
       if (e & 1) atomicOr(err, kErrOddPhase);
-      const int rv = (e >> 1) ^ (__popcll(st->mpiv[i] & R) & 1);
-      st->rV[i] = rv;
+      const int rv = (e >> 1) ^ (__popcll(sm[i] & R) & 1);
       R |= (uint64_t)rv << i;
     }
+    for (int i = 0; i < L; ++i) st->rV[i] = (int)((R >> i) & 1u);
   }
 }
 
@@ -652,11 +667,14 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
       blk_step_kernel<<<rb, 256, 0, s>>>(L.nrows, L.n, L.k, j, B, (j & 1) ? C1 : C0,
                                          (j & 1) ? C0 : C1, M, base, st);
   }
-  blk_vrows_kernel<<<chunks, kVrowThreads, kVrowSmem, s>>>(d.RX, d.RZ, L.rs, VX, VZ, st);
+  blk_vrows_kernel<<<dim3(chunks, kVrowSplit), kVrowThreads, kVrowSmem, s>>>(d.RX, d.RZ, L.rs, VX,
+                                                                              VZ, st);
   blk_signs_kernel<<<1, 64, 0, s>>>(d.S, st, d.err);
-  // about 8 waves of one block per SM (the table takes 200 KB of shared memory)
+  // about 8 waves of one block per SM (the table takes 200 KB of shared memory),
+  // but at least 512 rows per block so that building the 200 KB table stays
+  // small next to the rows it serves
   const uint32_t rows_y = std::max<uint32_t>(
-      1, (uint32_t)std::min<uint64_t>(((uint64_t)d.sms * 8 + chunks - 1) / chunks, L.nrows / 64 + 1));
+      1, (uint32_t)std::min<uint64_t>(((uint64_t)d.sms * 8 + chunks - 1) / chunks, L.nrows / 512));
   if ((uint64_t)L.nrows * L.rs < (1ull << 32))
     blk_apply_kernel<uint32_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
         d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, M, base, Tp, st);
