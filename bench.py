@@ -317,6 +317,8 @@ def run_ours(args):
 
     clocks = clk.summary()
     power = clk.mean_power_w()
+    # X and Z of one layout: 2 x ceil(n/256)*256 columns x ceil(2 ceil(n/64)/4)*4 words
+    tab_gb = 2 * ((n + 255) // 256 * 256) * ((2 * ((n + 63) // 64) + 3) // 4 * 4) * 8 / 1e9
     energy = None
     if power is not None:
         j_step = power * total_ms_max / args.steps / 1e3
@@ -349,8 +351,9 @@ def run_ours(args):
             "shots_per_step": shots,
             "fused_segments": fused,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-            "l2": ("inputs larger than L2 (tableau 16.2 GB in each layout)" if n >= 20_000
-                   else "tableau smaller than L2 (no flush: L2-resident by design)"),
+            "l2": (f"inputs larger than L2 (tableau {tab_gb:.3g} GB in each layout)" if tab_gb > 0.129
+                   else f"tableau ({tab_gb * 1e3:.3g} MB per layout) smaller than L2 "
+                        f"(no flush: L2-resident by design)"),
         },
         "phases": {
             "gate_layers": {"gates_per_s": gates_step * args.steps / (gate_ms / 1e3),
