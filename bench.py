@@ -518,8 +518,8 @@ def cpu_baseline(args, circ):
     mrate, mdt = oracle_measure_rate(args.cpu_meas_n, 40, args.cpu_meas_count)
     return {"value": rate, "unit": "gates/s", "cores": 1, "kind": "oracle",
             "sample": f"{args.cpu_rows} of {2 * circ.n} generator rows through the first "
-                      f"{args.cpu_layers} layers ({g} gates) of the 180k circuit, scaled by "
-                      f"2n/rows ({dt:.1f} s of CPU)",
+                      f"{args.cpu_layers} layers ({g} gates) of the workload's {circ.n}-qubit "
+                      f"circuit, scaled by 2n/rows ({dt:.1f} s of CPU)",
             "measurements_per_s": mrate,
             "measurements_sample": f"first {args.cpu_meas_count} final measurements after 40 "
                                    f"layers of the same generator at n={args.cpu_meas_n} "
@@ -589,6 +589,9 @@ def run_batch(args):
     identical = all(np.array_equal(s_.record(), b.record(i)) for s_, i in zip(sims, idx))
     g_sub = sum(c.n_gates for c in sub)
     m_sub = sum(c.n_measurements for c in sub)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = batch_cpu_baseline(circs, seeds)
     out = {"metric": "batched Clifford circuits: gates/s and measurements/s, one persistent "
                      "launch vs one circuit at a time",
            "value": gates / (ms_batch / 1e3), "unit": "gates/s", "n_gpus": 1,
@@ -603,8 +606,32 @@ def run_batch(args):
            "subset": {"circuits": len(sub), "gates": g_sub, "measurements": m_sub,
                       "batch_ms": ms_batch_sub, "one_at_a_time_ms": ms_single_sub,
                       "speedup": ms_single_sub / ms_batch_sub,
-                      "records_identical": bool(identical)}}
+                      "records_identical": bool(identical)},
+           "cpu_baseline": cpu}
     print(json.dumps(out))
+
+
+def batch_cpu_baseline(circs, seeds, budget_s: float = 15.0):
+    """The oracle on a seeded 32-circuit subset of the batch (every 16th
+    circuit), smallest first, until about `budget_s` seconds of one core are
+    spent: gates/s and measurements/s over the circuits it completed."""
+    from oracle import oracle as O
+    sub = sorted(range(0, len(circs), max(1, len(circs) // 32)), key=lambda i: circs[i].n)
+    g = m = 0
+    t0 = time.perf_counter()
+    done = []
+    for i in sub:
+        if time.perf_counter() - t0 > budget_s:
+            break
+        O.run_circuit(circs[i], seed=seeds[i])
+        g += circs[i].n_gates
+        m += circs[i].n_measurements
+        done.append(circs[i].n)
+    dt = time.perf_counter() - t0
+    return {"value": g / dt, "unit": "gates/s", "cores": 1, "kind": "oracle",
+            "measurements_per_s": m / dt,
+            "sample": f"{len(done)} circuits (n {min(done)}..{max(done)}) of a 32-circuit subset "
+                      f"(every 16th), smallest first, {dt:.1f} s of CPU"}
 
 
 def run_serve(args):
@@ -655,7 +682,24 @@ def run_serve(args):
            "saturation": sat, "saturation_rate_hz": sat_rate, "sweep": sweep,
            "one_at_a_time": one, "speedup_vs_one_at_a_time": one["makespan_s"] / sat["makespan_s"],
            "records_identical_alone_and_mixed": bool(same)}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = serve_cpu_baseline(specs, circs)
     print(json.dumps(out))
+
+
+def serve_cpu_baseline(specs, circs, shots: int = 20000):
+    """The oracle serving the smallest request: its reference shot plus
+    `shots` frame-sampled shots, timed on one core (shots/s)."""
+    from oracle import oracle as O
+    i = min(range(len(specs)), key=lambda j: circs[j].n)
+    c = circs[i]
+    t0 = time.perf_counter()
+    _, ref, _ = O.run_circuit(c, seed=specs[i].seed)
+    O.frames(c, ref, shots, seed=specs[i].seed + 1)
+    dt = time.perf_counter() - t0
+    return {"value": shots / dt, "unit": "shots/s", "cores": 1, "kind": "oracle",
+            "sample": f"request {i} (n={c.n}, depth {c.n_layers}): reference shot + {shots} "
+                      f"frame shots, {dt:.1f} s of CPU"}
 
 
 def run_reference(args):
