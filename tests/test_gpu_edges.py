@@ -1,0 +1,64 @@
+"""Degenerate inputs through the C ABI on the GPU: one qubit, empty layers and
+measurement lists, sampling a program without measurements, batches with
+empty circuits; every result against the oracle."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2603_14641_gb300 import qs  # noqa: E402
+from workloads import circuits as C  # noqa: E402
+
+
+def test_one_qubit_and_empty_operations():
+    sim = qs.Simulator(1, device="cuda:0")
+    sim.apply_layer(np.zeros((0, 3), np.uint32))                  # empty layer
+    assert len(sim.measure(np.zeros(0, np.uint32), seed=1)) == 0   # empty measurement list
+    sim.apply_layer(np.array([[C.H, 0, 0]], np.uint32))
+    out = sim.measure(np.array([0, 0, 0], np.uint32), seed=9)      # random, then repeated
+    o = O.Oracle(1)
+    o.apply(np.array([[C.H, 0, 0]], np.uint32))
+    oout, kinds = o.measure(np.array([0, 0, 0], np.uint32), seed=9)
+    assert np.array_equal(out, oout) and list(kinds) == [1, 0, 0]
+    assert out[0] == out[1] == out[2]
+    x, z, r = sim.export()
+    ox, oz, orr = o.get()
+    assert np.array_equal(x, ox) and np.array_equal(z, oz) and np.array_equal(r, orr)
+    sim.sync()
+
+
+def test_sampling_without_measurements_and_one_shot():
+    circ = C.random_circuit(50, 6, 0.5, seed=3, final_measure_all=False)
+    sim = qs.Simulator(50, device="cuda:0")
+    sim.run(circ, seed=2)
+    assert sim.num_measurements == 0
+    w = sim.sample(100, seed=4, on_device=False)
+    assert w.shape == (0, 2)
+    sim.measure(np.array([7], np.uint32), seed=2)
+    w = sim.sample(1, seed=4, on_device=False)
+    full = C.Circuit(n=50, gates=circ.gates, layer_ptr=circ.layer_ptr,
+                     ops=list(circ.ops) + [("measure", np.array([7], np.uint32))])
+    _, orec, _ = O.run_circuit(full, seed=2)
+    assert np.array_equal(sim.record(), orec)
+    ref = O.frames(full, orec, 1, seed=4)
+    assert w.shape == (1, 1) and int(w[0, 0]) >> 1 == 0 and (int(w[0, 0]) & 1) == ref[0, 0]
+
+
+def test_batch_with_empty_and_measure_only_circuits():
+    empty = C.Circuit(n=3, gates=np.zeros((0, 3), np.uint32), layer_ptr=np.array([0]), ops=[])
+    meas_only = C.Circuit(n=5, gates=np.zeros((0, 3), np.uint32), layer_ptr=np.array([0]),
+                          ops=[("measure", np.array([4, 0, 4], np.uint32))])
+    big_meas_only = C.Circuit(n=1100, gates=np.zeros((0, 3), np.uint32), layer_ptr=np.array([0]),
+                              ops=[("measure", np.arange(0, 1100, 50, dtype=np.uint32))])
+    normal = C.random_circuit(40, 8, 0.5, seed=6, measure_every=4, measure_frac=0.5)
+    circs = [empty, meas_only, big_meas_only, normal]
+    seeds = [1, 2, 3, 4]
+    b = qs.Batch(circs, seeds, device="cuda:0")
+    b.run()
+    b.sync()
+    for i, c in enumerate(circs):
+        _, orec, _ = O.run_circuit(c, seed=seeds[i])
+        assert np.array_equal(b.record(i), orec), i
+    assert not b.record(2).any()  # |0...0>: every outcome is 0
