@@ -255,6 +255,22 @@ int qs_sim_sample(qs_sim *sim, uint64_t shots, uint64_t seed, uint64_t *record,
 int qs_sim_tableau_export(qs_sim *sim, int layout, void *dst, size_t dst_bytes, size_t *needed);
 
 /*
+ * Restores a checkpoint (the paper has none; tableau, record and keys make one
+ * because the coins are keyed by record index): the tableau from a host
+ * buffer in qs_sim_tableau_export's layout and the first record_count record
+ * entries (0/1 bytes, host). Measurements after the import continue the
+ * record at index record_count, so with the same keys they reproduce the
+ * uninterrupted run bit for bit. The op log is cleared and qs_sim_sample is
+ * refused (QS_ERR_STATE) until qs_sim_reset: frame sampling replays the
+ * program from |0...0>. The tableau is not checked for validity beyond zero
+ * bits past qubit n - 1 (QS_ERR_ARG). Syncs.
+ * Errors: QS_ERR_ARG (layout, padding bits, NULL record), QS_ERR_SIZE
+ * (src_bytes too small, record_count above the record capacity).
+ */
+int qs_sim_tableau_import(qs_sim *sim, int layout, const void *src, size_t src_bytes,
+                          const uint8_t *record, uint64_t record_count);
+
+/*
  * Copies selected generator rows to host memory: rows[i] in 0..2n-1
  * (0..n-1 destabilizers D_i, n..2n-1 stabilizers S_i, Sec. 2.5 Eq. 7). For
  * each row dst receives ceil(n/64) x-words, ceil(n/64) z-words (bit j of word

@@ -113,6 +113,7 @@ struct qs_sim {
   uint64_t launches = 0;
   uint32_t flags = 0;
   void *blk = nullptr;  // scratch of the blocked measurement
+  bool resumed = false; // state restored by qs_sim_tableau_import: no op log from |0...0>
 };
 
 namespace {
@@ -357,6 +358,7 @@ int qs_sim_reset(qs_sim *s, const uint8_t *initstate) {
   s->n_meas = 0;
   s->n_noise = 0;
   s->ops.clear();
+  s->resumed = false;
   return QS_OK;
 }
 
@@ -650,6 +652,9 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
                   void *frame_ws, size_t frame_ws_bytes) {
   int rc = check_usable(s);
   if (rc) return rc;
+  if (s->resumed)
+    return fail(QS_ERR_STATE, "sampling replays the op log from |0...0>; a sim restored by "
+                              "qs_sim_tableau_import has none (qs_sim_reset first)");
   if (shots == 0) return fail(QS_ERR_ARG, "shots must be positive");
   uint64_t fw, ow;
   const size_t need = sample_bytes(s, shots, &fw, &ow);
@@ -771,6 +776,60 @@ int qs_sim_tableau_export(qs_sim *s, int layout, void *dst, size_t dst_bytes, si
   return QS_OK;
 }
 
+int qs_sim_tableau_import(qs_sim *s, int layout, const void *src, size_t src_bytes,
+                          const uint8_t *record, uint64_t record_count) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (layout != QS_LAYOUT_ROWS_PACKED) return fail(QS_ERR_ARG, "unknown layout");
+  const Layout &L = s->d.L;
+  const uint32_t n = L.n, k = L.k;
+  const size_t sw = (2ull * n + 63) / 64;
+  const size_t bytes = (2ull * n * 2 * k + sw) * 8;
+  if (!src || src_bytes < bytes) return fail(QS_ERR_SIZE, "import buffer smaller than the tableau");
+  if (record_count > s->d.record_cap)
+    return fail(QS_ERR_SIZE, "record capacity exceeded (qs_options.record_capacity)");
+  if (record_count && !record) return fail(QS_ERR_ARG, "record is NULL");
+  const uint64_t *in = static_cast<const uint64_t *>(src);
+  // bits of qubits >= n in the last word of each row must be zero
+  if (n & 63) {
+    const uint64_t pad = ~0ull << (n & 63);
+    for (uint64_t i = 0; i < 2ull * n; ++i)
+      if ((in[i * 2 * k + k - 1] | in[i * 2 * k + 2 * k - 1]) & pad)
+        return fail(QS_ERR_ARG, "row " + std::to_string(i) + " has bits beyond qubit n - 1");
+  }
+  const uint64_t *sig = in + 2ull * n * 2 * k;
+  std::vector<uint64_t> S(L.cs, 0);
+  for (uint64_t i = 0; i < 2ull * n; ++i) {
+    const uint64_t pr = i < n ? i : 64ull * k + (i - n);
+    if ((sig[i >> 6] >> (i & 63)) & 1u) S[pr >> 6] |= 1ull << (pr & 63);
+  }
+  const size_t rowb = (size_t)L.nrows * L.rs * 8;
+  QS_CUDA(s, cudaMemsetAsync(s->d.RX, 0, rowb, s->stream));
+  QS_CUDA(s, cudaMemsetAsync(s->d.RZ, 0, rowb, s->stream));
+  const size_t sp = 2ull * k * 8, dp = (size_t)L.rs * 8, wb = (size_t)k * 8;
+  const size_t st = 64ull * k * L.rs;
+  QS_CUDA(s, cudaMemcpy2DAsync(s->d.RX, dp, in, sp, wb, n, cudaMemcpyHostToDevice, s->stream));
+  QS_CUDA(s, cudaMemcpy2DAsync(s->d.RZ, dp, in + k, sp, wb, n, cudaMemcpyHostToDevice, s->stream));
+  QS_CUDA(s, cudaMemcpy2DAsync(s->d.RX + st, dp, in + (size_t)n * 2 * k, sp, wb, n,
+                               cudaMemcpyHostToDevice, s->stream));
+  QS_CUDA(s, cudaMemcpy2DAsync(s->d.RZ + st, dp, in + (size_t)n * 2 * k + k, sp, wb, n,
+                               cudaMemcpyHostToDevice, s->stream));
+  QS_CUDA(s, cudaMemcpyAsync(s->d.S, S.data(), (size_t)L.cs * 8, cudaMemcpyHostToDevice, s->stream));
+  if (record_count)
+    QS_CUDA(s, cudaMemcpyAsync(s->d.record, record, record_count, cudaMemcpyHostToDevice, s->stream));
+  QS_CUDA(s, cudaMemsetAsync(s->d.err, 0, 4, s->stream));
+  QS_CUDA(s, launch_reset_meas_state(s->d, s->stream));
+  s->launches += 1;
+  QS_CUDA(s, cudaStreamSynchronize(s->stream));  // the host buffers may go once this returns
+  s->rows_valid = true;
+  s->cols_valid = false;
+  s->n_meas = record_count;
+  s->n_noise = 0;
+  s->ops.clear();
+  s->resumed = true;
+  return QS_OK;
+}
+
 int qs_sim_export_rows(qs_sim *s, const uint32_t *rows, uint32_t count, uint64_t *dst) {
   int rc = check_usable(s);
   if (rc) return rc;
@@ -828,6 +887,9 @@ extern "C" int qs_sim_sample_noalloc(qs_sim *s, uint64_t shots, uint64_t seed, u
                                      size_t record_words) {
   int rc = check_usable(s);
   if (rc) return rc;
+  if (s->resumed)
+    return fail(QS_ERR_STATE, "sampling replays the op log from |0...0>; a sim restored by "
+                              "qs_sim_tableau_import has none (qs_sim_reset first)");
   if (shots == 0) return fail(QS_ERR_ARG, "shots must be positive");
   const uint32_t n = s->d.L.n;
   const uint64_t M = s->n_meas;

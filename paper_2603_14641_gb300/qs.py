@@ -83,6 +83,8 @@ SIGNATURES = {
     "qs_sim_measure": (ctypes.c_int, [_vp, _vp, _u32, qs_key, _vp]),
     "qs_sim_measure_dev": (ctypes.c_int, [_vp, _vp, _u32, qs_key]),
     "qs_sim_noise": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _vp, _u32]),
+    "qs_sim_tableau_import": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp,
+                                             ctypes.c_uint64]),
     "qs_sim_num_measurements": (_u64, [_vp]),
     "qs_sim_record": (ctypes.c_int, [_vp, _u64, _u64, _vp]),
     "qs_sim_sample_required_bytes": (_sz, [_vp, _u64]),
@@ -212,6 +214,16 @@ def qs_sim_measure(sim: int, qubits: np.ndarray, seed: int, shot: int = 0,
 def qs_sim_measure_dev(sim: int, qubits_dev: int, count: int, seed: int, shot: int = 0) -> None:
     _check(lib().qs_sim_measure_dev(ctypes.c_void_p(sim), ctypes.c_void_p(qubits_dev), count,
                                     qs_key(seed, shot)), "qs_sim_measure_dev")
+
+
+def qs_sim_tableau_import(sim: int, packed: np.ndarray, record: np.ndarray) -> None:
+    """Restores a checkpoint: `packed` as returned by qs_sim_tableau_export,
+    `record` the 0/1 record bytes so far."""
+    t = np.ascontiguousarray(packed, np.uint64)
+    r = np.ascontiguousarray(record, np.uint8)
+    _check(lib().qs_sim_tableau_import(ctypes.c_void_p(sim), QS_LAYOUT_ROWS_PACKED,
+                                       t.ctypes.data, t.nbytes, r.ctypes.data if len(r) else None,
+                                       len(r)), "qs_sim_tableau_import")
 
 
 def qs_sim_noise(sim: int, kind: int, p: float, targets) -> None:
@@ -357,6 +369,13 @@ class Simulator:
     def measure_dev(self, qubits_dev, seed: int, shot: int = 0):
         self._keep.append(qubits_dev)
         qs_sim_measure_dev(self.sim, qubits_dev.data_ptr(), qubits_dev.numel(), seed, shot)
+
+    def checkpoint(self):
+        """(packed tableau, record): everything a later run needs to resume."""
+        return qs_sim_tableau_export(self.sim), self.record()
+
+    def restore(self, packed, record):
+        qs_sim_tableau_import(self.sim, packed, record)
 
     def noise(self, kind: int, p: float, targets):
         """Appends a Pauli noise channel (QS_NOISE_*) for the sampled shots."""
