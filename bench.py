@@ -285,6 +285,7 @@ def run_ours(args):
         barrier(ws)
     launches = qs.qs_sim_launch_count(sim.sim) - launches0
     qs.qs_sim_sync(sim.sim)  # device self-checks
+    kinds = qs.qs_sim_record_kinds(sim.sim) if M else np.zeros(0, np.uint8)  # last step's record
     total_ms = start.elapsed_time(end)
     ph = {"layers": 0.0, "measure": 0.0, "sample": 0.0}
     for ev in evs:
@@ -360,6 +361,8 @@ def run_ours(args):
                             "ms_per_step": gate_ms / args.steps},
             "measurement": {"measurements_per_s": M * args.steps / (meas_ms / 1e3) if M else None,
                             "ms_per_step": meas_ms / args.steps,
+                            "probabilistic": int((kinds == 1).sum()),
+                            "deterministic": int((kinds == 0).sum()),
                             "includes": "column->row layout switch (2 transposes) per window"},
             "sampling": {"shots_per_s": shots * args.steps / (samp_ms / 1e3),
                          "ms_per_step": samp_ms / args.steps,

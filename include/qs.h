@@ -189,6 +189,11 @@ uint64_t qs_sim_num_measurements(const qs_sim *sim);
 /* Copies record entries [first, first + count) to host bytes (0/1). Syncs. */
 int qs_sim_record(qs_sim *sim, uint64_t first, uint64_t count, uint8_t *dst);
 
+/* Kind of each record entry [first, first + count) as host bytes: 1 = the
+ * outcome was probabilistic (a pivot existed, the outcome is the coin), 0 =
+ * deterministic (Sec. 2.5), 2 = restored by qs_sim_tableau_import. Syncs. */
+int qs_sim_record_kinds(qs_sim *sim, uint64_t first, uint64_t count, uint8_t *dst);
+
 /* Pauli noise channels of qs_sim_noise (the values are part of the ABI). */
 enum {
   QS_NOISE_X = 0,           /* X with probability p */

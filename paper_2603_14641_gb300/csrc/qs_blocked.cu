@@ -565,12 +565,14 @@ blk_rows_kernel(uint64_t *__restrict__ S, uint64_t nrows, const uint32_t *__rest
                 const uint64_t *__restrict__ M, const int32_t *__restrict__ base,
                 const int32_t *__restrict__ Tp, uint32_t chunks, const BlkState *st, uint64_t m0,
                 uint64_t seed,
-                uint64_t shot, uint8_t *__restrict__ record, uint32_t *__restrict__ err) {
+                uint64_t shot, uint8_t *__restrict__ record, uint8_t *__restrict__ kinds,
+                uint32_t *__restrict__ err) {
   const int L = st->len;
   const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r < (uint64_t)L) {
     const uint32_t b = (uint32_t)(philox4x64_10(m0 + r, shot, 0, 0, seed, kCoinKey).v[0] & 1u);
     record[m0 + r] = (uint8_t)b;
+    kinds[m0 + r] = 1;  // every step of a block had a pivot
   }
   uint64_t delta = 0;
   if (r < nrows && L > 0) {
@@ -682,7 +684,7 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
     blk_apply_kernel<uint64_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
         d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, M, base, Tp, st);
   blk_rows_kernel<<<rb, 256, 0, s>>>(d.S, L.nrows, qubits, M, base, Tp, chunks, st, m0, key.seed,
-                                     key.shot, d.record, d.err);
+                                     key.shot, d.record, d.kinds, d.err);
   if (launches) *launches += 6 + sym_launches;
   if (len_dev) *len_dev = &st->len;
   return cudaGetLastError();

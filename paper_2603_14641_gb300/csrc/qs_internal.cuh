@@ -115,6 +115,7 @@ struct Dev {
   int32_t *det_scal;       // kDetBlocks partial phase sums
   uint32_t *err;           // sticky error flags
   uint8_t *record;         // record bytes
+  uint8_t *kinds;          // per record entry: 1 probabilistic, 0 deterministic, 2 restored
   uint64_t record_cap;
   int sms;                 // multiprocessor count of the device
 };

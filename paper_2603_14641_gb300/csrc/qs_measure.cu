@@ -241,12 +241,18 @@ finalize_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t r
                 uint32_t k, uint64_t *__restrict__ S, int64_t *__restrict__ mst,
                 const uint32_t *__restrict__ qubits, uint32_t qi, uint64_t midx, uint64_t seed,
                 uint64_t shot, const int32_t *__restrict__ det_scal, uint32_t nchunks,
-                uint8_t *__restrict__ record, uint32_t *__restrict__ err) {
+                uint8_t *__restrict__ record, uint8_t *__restrict__ kinds,
+                uint32_t *__restrict__ err) {
   const uint32_t q = qubits[qi];
   const int64_t p = mst[kMsPivot];
   __syncthreads();
   if (q >= n) {
-    if (threadIdx.x == 0) { record[midx] = 0; mst[kMsPivot] = kNoPivot; mst[kMsDetCross] = 0; }
+    if (threadIdx.x == 0) {
+      record[midx] = 0;
+      kinds[midx] = 0;
+      mst[kMsPivot] = kNoPivot;
+      mst[kMsDetCross] = 0;
+    }
     return;
   }
   if (p != kNoPivot) {
@@ -264,6 +270,7 @@ finalize_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t r
       S[pd >> 6] = (S[pd >> 6] & ~(1ull << (pd & 63))) | (sp << (pd & 63));
       S[p >> 6] = (S[p >> 6] & ~(1ull << (p & 63))) | ((uint64_t)b << (p & 63));
       record[midx] = (uint8_t)b;
+      kinds[midx] = 1;
     }
   } else if (threadIdx.x == 0) {
     int t = 0;
@@ -272,6 +279,7 @@ finalize_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t r
     t = mod4(t);
     if (t & 1) atomicOr(err, kErrOddPhase);
     record[midx] = (uint8_t)(t >> 1);
+    kinds[midx] = 0;
   }
   if (threadIdx.x == 0) { mst[kMsPivot] = kNoPivot; mst[kMsDetCross] = 0; }
 }
@@ -317,7 +325,7 @@ cudaError_t launch_measure_one(const Dev &d, const uint32_t *qubits, uint32_t i,
   det_combine_kernel<<<(L.k + 255) / 256, 256, 0, s>>>(L.rs, L.n, L.k, d.mst, qubits, i,
                                                        d.det_x, d.det_z, nchunks, d.err);
   finalize_kernel<<<1, 256, 0, s>>>(d.RX, d.RZ, L.rs, L.n, L.k, d.S, d.mst, qubits, i, midx,
-                                    key.seed, key.shot, d.det_scal, nchunks, d.record, d.err);
+                                    key.seed, key.shot, d.det_scal, nchunks, d.record, d.kinds, d.err);
   if (launches) *launches += 5;
   return cudaGetLastError();
 }
@@ -467,7 +475,8 @@ meas_finalize_gather_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ
                             uint64_t midx, uint64_t seed, uint64_t shot,
                             const uint64_t *__restrict__ det_x, const uint64_t *__restrict__ det_z,
                             const int32_t *__restrict__ det_scal, uint32_t nchunks,
-                            uint8_t *__restrict__ record, uint32_t *__restrict__ err) {
+                            uint8_t *__restrict__ record, uint8_t *__restrict__ kinds,
+                            uint32_t *__restrict__ err) {
   const int slot = j & 1;
   const int64_t p = mst[slot];
   const uint32_t q = qubits[j];
@@ -504,7 +513,7 @@ meas_finalize_gather_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ
   if (blockIdx.x != 0) return;
   // finalize measurement j (block 0)
   if (q >= n) {
-    if (threadIdx.x == 0) { record[midx] = 0; atomicOr(err, kErrBadQubit); }
+    if (threadIdx.x == 0) { record[midx] = 0; kinds[midx] = 0; atomicOr(err, kErrBadQubit); }
     return;
   }
   if (prob) {
@@ -521,6 +530,7 @@ meas_finalize_gather_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ
       S[pd >> 6] = (S[pd >> 6] & ~(1ull << (pd & 63))) | (sp << (pd & 63));
       S[p >> 6] = (S[p >> 6] & ~(1ull << (p & 63))) | ((uint64_t)b << (p & 63));
       record[midx] = (uint8_t)b;
+      kinds[midx] = 1;
     }
     return;
   }
@@ -548,6 +558,7 @@ meas_finalize_gather_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ
     if (t & 1) atomicOr(err, kErrOddPhase);
     if (s_bad) atomicOr(err, kErrDetProduct);
     record[midx] = (uint8_t)(t >> 1);
+    kinds[midx] = 0;
   }
 }
 
@@ -597,7 +608,7 @@ cudaError_t launch_measure_window(const Dev &d, const uint32_t *qubits, uint32_t
     else launch_update_t<16>(d, rblocks, smem, qubits, j, has_next, nchunks, s);
     meas_finalize_gather_kernel<<<gblocks, 256, 0, s>>>(
         d.RX, d.RZ, L.rs, L.nrows, L.n, L.k, d.S, d.colx, d.mst, qubits, j, has_next, m0 + j,
-        key.seed, key.shot, d.det_x, d.det_z, d.det_scal, nchunks, d.record, d.err);
+        key.seed, key.shot, d.det_x, d.det_z, d.det_scal, nchunks, d.record, d.kinds, d.err);
     l += 2;
   }
   if (launches) *launches += l;

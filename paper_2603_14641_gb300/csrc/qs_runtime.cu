@@ -59,7 +59,7 @@ struct Carve {
 };
 
 struct Plan {
-  size_t X, Z, RX, RZ, S, colx, mst, detx, detz, dets, err, record, stage, blk, total;
+  size_t X, Z, RX, RZ, S, colx, mst, detx, detz, dets, err, record, kinds, stage, blk, total;
   uint64_t record_cap;
   size_t stage_bytes;
 };
@@ -82,6 +82,7 @@ Plan make_plan(const Layout &L, const qs_options *opt) {
   p.dets = c.take((size_t)kDetBlocks * 4);
   p.err = c.take(4);
   p.record = c.take(p.record_cap);
+  p.kinds = c.take(p.record_cap);
   p.stage = c.take(p.stage_bytes);
   p.blk = c.take(blocked_scratch_bytes(L));
   p.total = c.off;
@@ -298,6 +299,7 @@ int qs_sim_create(uint32_t n, const qs_options *opt, void *cuda_stream, void *wo
   s->d.det_scal = reinterpret_cast<int32_t *>(b + p.dets);
   s->d.err = reinterpret_cast<uint32_t *>(b + p.err);
   s->d.record = b + p.record;
+  s->d.kinds = b + p.kinds;
   s->d.record_cap = p.record_cap;
   s->dstage = b + p.stage;
   s->blk = b + p.blk;
@@ -579,6 +581,16 @@ int qs_sim_record(qs_sim *s, uint64_t first, uint64_t count, uint8_t *dst) {
   return qs_sim_sync(s);
 }
 
+int qs_sim_record_kinds(qs_sim *s, uint64_t first, uint64_t count, uint8_t *dst) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (first + count > s->n_meas) return fail(QS_ERR_ARG, "record range beyond the measurements");
+  if (count && !dst) return fail(QS_ERR_ARG, "dst is NULL");
+  if (count)
+    QS_CUDA(s, cudaMemcpyAsync(dst, s->d.kinds + first, count, cudaMemcpyDeviceToHost, s->stream));
+  return qs_sim_sync(s);
+}
+
 int qs_sim_sync(qs_sim *s) {
   if (!s) return fail(QS_ERR_ARG, "sim is NULL");
   if (s->broken) return fail(QS_ERR_STATE, "sim is unusable after an earlier device error");
@@ -815,8 +827,10 @@ int qs_sim_tableau_import(qs_sim *s, int layout, const void *src, size_t src_byt
   QS_CUDA(s, cudaMemcpy2DAsync(s->d.RZ + st, dp, in + (size_t)n * 2 * k + k, sp, wb, n,
                                cudaMemcpyHostToDevice, s->stream));
   QS_CUDA(s, cudaMemcpyAsync(s->d.S, S.data(), (size_t)L.cs * 8, cudaMemcpyHostToDevice, s->stream));
-  if (record_count)
+  if (record_count) {
     QS_CUDA(s, cudaMemcpyAsync(s->d.record, record, record_count, cudaMemcpyHostToDevice, s->stream));
+    QS_CUDA(s, cudaMemsetAsync(s->d.kinds, 2, record_count, s->stream));
+  }
   QS_CUDA(s, cudaMemsetAsync(s->d.err, 0, 4, s->stream));
   QS_CUDA(s, launch_reset_meas_state(s->d, s->stream));
   s->launches += 1;

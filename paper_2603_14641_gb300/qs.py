@@ -83,6 +83,7 @@ SIGNATURES = {
     "qs_sim_measure": (ctypes.c_int, [_vp, _vp, _u32, qs_key, _vp]),
     "qs_sim_measure_dev": (ctypes.c_int, [_vp, _vp, _u32, qs_key]),
     "qs_sim_noise": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _vp, _u32]),
+    "qs_sim_record_kinds": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint64, _vp]),
     "qs_sim_tableau_import": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_size_t, _vp,
                                              ctypes.c_uint64]),
     "qs_sim_num_measurements": (_u64, [_vp]),
@@ -241,6 +242,16 @@ def qs_sim_record(sim: int, first: int = 0, count: Optional[int] = None) -> np.n
         count = qs_sim_num_measurements(sim) - first
     out = np.zeros(max(count, 1), np.uint8)
     _check(lib().qs_sim_record(ctypes.c_void_p(sim), first, count, _ptr(out)), "qs_sim_record")
+    return out[:count]
+
+
+def qs_sim_record_kinds(sim: int, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+    """1 = probabilistic, 0 = deterministic, 2 = restored from a checkpoint."""
+    if count is None:
+        count = qs_sim_num_measurements(sim) - first
+    out = np.zeros(max(count, 1), np.uint8)
+    _check(lib().qs_sim_record_kinds(ctypes.c_void_p(sim), first, count, _ptr(out)),
+           "qs_sim_record_kinds")
     return out[:count]
 
 
@@ -403,6 +414,9 @@ class Simulator:
 
     def record(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
         return qs_sim_record(self.sim, first, count)
+
+    def record_kinds(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        return qs_sim_record_kinds(self.sim, first, count)
 
     def export(self):
         return unpack_rows(qs_sim_tableau_export(self.sim), self.n)

@@ -384,6 +384,34 @@ def test_blocked_matches_unblocked(n):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("n,flags", [(300, 0), (300, qs.QS_FLAG_UNPIPELINED_MEASURE),
+                                     (1100, 0), (1100, qs.QS_FLAG_NO_BLOCKED_MEASURE),
+                                     (30000, 0)])
+def test_measurement_kinds_match_oracle(n, flags):
+    """Probabilistic / deterministic kind of every record entry, through the
+    blocked, pipelined and five-launch paths, against the oracle's kinds."""
+    depth = 10
+    circ = C.random_circuit(n, depth, 0.5, seed=n + flags, final_measure_all=False)
+    rng = np.random.default_rng(n)
+    q = rng.permutation(n)[:min(n, 120)].astype(np.uint32)
+    q = np.concatenate([q[:40], q[:10], q[40:]])  # repeats: deterministic outcomes
+    sim = _sim(n, flags=flags)
+    dc = sim.upload(circ)
+    sim.apply_layers_dev(dc, 0, depth)
+    rec = sim.measure(q, seed=4)
+    kinds = sim.record_kinds()
+    if n <= 2000:
+        o = O.Oracle(n)
+        o.apply(circ.gates)
+        orec, okinds = o.measure(q, seed=4)
+        assert np.array_equal(rec, orec)
+        assert np.array_equal(kinds, okinds)
+    else:  # the repeated qubits are deterministic, the first measurements of a dense state are not
+        assert (kinds[40:50] == 0).all() and np.array_equal(rec[40:50], rec[:10])
+        assert set(np.unique(kinds)) <= {0, 1}
+    sim.sync()
+
+
 def test_qasm_front_end_end_to_end():
     """OpenQASM text over the 11-gate set with interleaved measurements,
     scheduled into windows (Sec. 4.2), run on the GPU against the oracle."""
