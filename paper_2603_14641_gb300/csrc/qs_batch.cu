@@ -35,6 +35,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qs_internal.cuh"
 #include "qs_rules.cuh"
 
@@ -994,6 +996,7 @@ static int tuning_ok(const qs_batch *b, const qs_batch_tuning &t, size_t *smem) 
 }
 
 static int run_kernel(qs_batch *b, const qs_batch_tuning *tuning, uint32_t round_limit);
+static int batch_run(qs_batch *b, const qs_batch_tuning *tuning, uint32_t round_limit);
 
 // Enqueues every large circuit's rounds on its simulator, one host thread per
 // worker stream (blocked measurement waits for its stream once per block),
@@ -1050,6 +1053,13 @@ static int run_sims(qs_batch *b, uint32_t round_limit) {
 }
 
 int qs_batch_run(qs_batch *b, const qs_batch_tuning *tuning, uint32_t round_limit) {
+  nvtxRangePushA("qs_batch_run");
+  const int rc = batch_run(b, tuning, round_limit);
+  nvtxRangePop();
+  return rc;
+}
+
+static int batch_run(qs_batch *b, const qs_batch_tuning *tuning, uint32_t round_limit) {
   if (!b) return bfail(QS_ERR_ARG, "batch is NULL");
   if (b->broken) return bfail(QS_ERR_STATE, "batch is unusable after an earlier device error");
   int rc = QS_OK;

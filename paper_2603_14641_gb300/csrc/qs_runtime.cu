@@ -18,6 +18,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qs_internal.cuh"
 
 using namespace qs;
@@ -25,6 +27,12 @@ using namespace qs;
 namespace {
 
 thread_local std::string g_last_error;
+
+// NVTX range over one ABI call (shows in Nsight timelines; no cost without a tool)
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 int fail(int code, const std::string &msg) {
   g_last_error = msg;
@@ -365,6 +373,7 @@ int qs_sim_reset(qs_sim *s, const uint8_t *initstate) {
 }
 
 int qs_sim_apply_layer(qs_sim *s, const qs_gate *gates, uint32_t n_gates) {
+  Range range_("qs_sim_apply_layer");
   int rc = check_usable(s);
   if (rc) return rc;
   if (n_gates && !gates) return fail(QS_ERR_ARG, "gates is NULL");
@@ -412,6 +421,7 @@ int qs_pack_layers(uint32_t n, const qs_gate *gates, const int64_t *layer_ptr, u
 
 int qs_sim_apply_layers_dev(qs_sim *s, const uint32_t *packed_dev, const int64_t *layer_ptr,
                             uint32_t l_begin, uint32_t l_end) {
+  Range range_("qs_sim_apply_layers_dev");
   int rc = check_usable(s);
   if (rc) return rc;
   if (!packed_dev || !layer_ptr) return fail(QS_ERR_ARG, "NULL argument");
@@ -441,6 +451,7 @@ static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint6
     // outcome, which then goes through the single-measurement path
     uint32_t i = 0;
     while (i < count) {
+      Range block_range("blocked measurement block");
       const int B = (int)std::min<uint32_t>(64, count - i);
       int l = 0;
       int32_t *len_dev = nullptr;
@@ -476,6 +487,7 @@ static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint6
 
 int qs_sim_measure(qs_sim *s, const uint32_t *qubits, uint32_t count, qs_key key,
                    uint8_t *outcomes) {
+  Range range_("qs_sim_measure");
   int rc = check_usable(s);
   if (rc) return rc;
   if (count && !qubits) return fail(QS_ERR_ARG, "qubits is NULL");
@@ -516,6 +528,7 @@ int qs_sim_measure(qs_sim *s, const uint32_t *qubits, uint32_t count, qs_key key
 }
 
 int qs_sim_measure_dev(qs_sim *s, const uint32_t *qubits_dev, uint32_t count, qs_key key) {
+  Range range_("qs_sim_measure_dev");
   int rc = check_usable(s);
   if (rc) return rc;
   if (count && !qubits_dev) return fail(QS_ERR_ARG, "qubits_dev is NULL");
@@ -662,6 +675,7 @@ static bool is_device_ptr(const void *p) {
 
 int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, size_t record_words,
                   void *frame_ws, size_t frame_ws_bytes) {
+  Range range_("qs_sim_sample");
   int rc = check_usable(s);
   if (rc) return rc;
   if (s->resumed)
@@ -756,6 +770,7 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
 }
 
 int qs_sim_tableau_export(qs_sim *s, int layout, void *dst, size_t dst_bytes, size_t *needed) {
+  Range range_("qs_sim_tableau_export");
   int rc = check_usable(s);
   if (rc) return rc;
   if (layout != QS_LAYOUT_ROWS_PACKED) return fail(QS_ERR_ARG, "unknown layout");
@@ -790,6 +805,7 @@ int qs_sim_tableau_export(qs_sim *s, int layout, void *dst, size_t dst_bytes, si
 
 int qs_sim_tableau_import(qs_sim *s, int layout, const void *src, size_t src_bytes,
                           const uint8_t *record, uint64_t record_count) {
+  Range range_("qs_sim_tableau_import");
   int rc = check_usable(s);
   if (rc) return rc;
   if (layout != QS_LAYOUT_ROWS_PACKED) return fail(QS_ERR_ARG, "unknown layout");
@@ -899,6 +915,7 @@ uint64_t g_noalloc_seen[(kMaxQubits + 63) / 64];
 
 extern "C" int qs_sim_sample_noalloc(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record,
                                      size_t record_words) {
+  Range range_("qs_sim_sample_noalloc");
   int rc = check_usable(s);
   if (rc) return rc;
   if (s->resumed)
