@@ -54,7 +54,7 @@ struct Op {
 
 constexpr int kRing = 4;
 constexpr uint32_t kBlockedMinCount = 16;    // windows this long use blocked measurement
-constexpr uint32_t kBlockedMinQubits = 1024;
+constexpr uint32_t kBlockedMinQubits = 64;
 constexpr uint32_t kMaxQubits = 1u << 20;
 
 struct Carve {
@@ -448,9 +448,17 @@ static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint6
   if (!(s->flags & (QS_FLAG_UNPIPELINED_MEASURE | QS_FLAG_NO_BLOCKED_MEASURE)) &&
       measure_window_supported(s->d.L) && count >= kBlockedMinCount && s->d.L.n >= kBlockedMinQubits) {
     // blocks of up to 64 measurements; a block stops before a deterministic
-    // outcome, which then goes through the single-measurement path
-    uint32_t i = 0;
+    // outcome, which then goes through the single-measurement path. After two
+    // blocks in a row that stop at their first step (a run of deterministic
+    // outcomes), the rest of the window takes the pipelined path.
+    uint32_t i = 0, empty_blocks = 0;
     while (i < count) {
+      if (empty_blocks >= 2) {
+        int l = 0;
+        QS_CUDA(s, launch_measure_window(s->d, qdev + i, count - i, m0 + i, key, s->stream, &l));
+        s->launches += (uint64_t)l;
+        break;
+      }
       Range block_range("blocked measurement block");
       const int B = (int)std::min<uint32_t>(64, count - i);
       int l = 0;
@@ -468,6 +476,7 @@ static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint6
         s->launches += (uint64_t)l;
         i += 1;
       }
+      empty_blocks = done == 0 ? empty_blocks + 1 : 0;
     }
     return QS_OK;
   }
