@@ -158,7 +158,11 @@ int qs_pack_layers(uint32_t n, const qs_gate *gates, const int64_t *layer_ptr, u
  * memory (packed by qs_pack_layers for this n and copied to the device by the
  * caller). packed_dev must stay valid until the work has run and, if
  * qs_sim_sample will replay it, until the sim is reset or destroyed.
- * layer_ptr: host offsets as given to qs_pack_layers.
+ * layer_ptr: host offsets as given to qs_pack_layers (layer l of the call is
+ *            packed_dev gate records [layer_ptr[l], layer_ptr[l+1])).
+ * Errors: QS_ERR_ARG (NULL argument, l_end < l_begin, a negative or
+ * decreasing offset, a layer of more than n gates); gate records that are
+ * invalid on the device are skipped and raise QS_ERR_INTERNAL at the next sync.
  */
 int qs_sim_apply_layers_dev(qs_sim *sim, const uint32_t *packed_dev, const int64_t *layer_ptr,
                             uint32_t l_begin, uint32_t l_end);

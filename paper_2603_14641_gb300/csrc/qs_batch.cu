@@ -1145,6 +1145,7 @@ int qs_batch_sync(qs_batch *b) {
 int qs_batch_record(qs_batch *b, uint32_t circuit, uint8_t *dst, size_t count) {
   if (!b || circuit >= b->count) return bfail(QS_ERR_ARG, "bad batch or circuit index");
   if (count > b->meas_total[circuit]) return bfail(QS_ERR_ARG, "count beyond the circuit's record");
+  if (count && !dst) return bfail(QS_ERR_ARG, "dst is NULL");
   int rc = qs_batch_sync(b);
   if (rc) return rc;
   if (b->sim_of[circuit] >= 0) {

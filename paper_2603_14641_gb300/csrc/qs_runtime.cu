@@ -432,6 +432,7 @@ int qs_sim_apply_layers_dev(qs_sim *s, const uint32_t *packed_dev, const int64_t
   op.kind = Op::kDevLayers;
   op.dev = packed_dev;
   op.ptr.assign(layer_ptr + l_begin, layer_ptr + l_end + 1);
+  if (op.ptr[0] < 0) return fail(QS_ERR_ARG, "negative layer_ptr");
   for (size_t l = 0; l + 1 < op.ptr.size(); ++l) {
     const int64_t cnt = op.ptr[l + 1] - op.ptr[l];
     if (cnt < 0 || cnt > (int64_t)s->d.L.n) return fail(QS_ERR_ARG, "bad layer_ptr");
@@ -596,7 +597,8 @@ uint64_t qs_sim_launch_count(const qs_sim *s) { return s ? s->launches : 0; }
 int qs_sim_record(qs_sim *s, uint64_t first, uint64_t count, uint8_t *dst) {
   int rc = check_usable(s);
   if (rc) return rc;
-  if (first + count > s->n_meas) return fail(QS_ERR_ARG, "record range beyond the measurements");
+  if (first > s->n_meas || count > s->n_meas - first)
+    return fail(QS_ERR_ARG, "record range beyond the measurements");
   if (count && !dst) return fail(QS_ERR_ARG, "dst is NULL");
   if (count)
     QS_CUDA(s, cudaMemcpyAsync(dst, s->d.record + first, count, cudaMemcpyDeviceToHost, s->stream));
@@ -606,7 +608,8 @@ int qs_sim_record(qs_sim *s, uint64_t first, uint64_t count, uint8_t *dst) {
 int qs_sim_record_kinds(qs_sim *s, uint64_t first, uint64_t count, uint8_t *dst) {
   int rc = check_usable(s);
   if (rc) return rc;
-  if (first + count > s->n_meas) return fail(QS_ERR_ARG, "record range beyond the measurements");
+  if (first > s->n_meas || count > s->n_meas - first)
+    return fail(QS_ERR_ARG, "record range beyond the measurements");
   if (count && !dst) return fail(QS_ERR_ARG, "dst is NULL");
   if (count)
     QS_CUDA(s, cudaMemcpyAsync(dst, s->d.kinds + first, count, cudaMemcpyDeviceToHost, s->stream));
@@ -704,6 +707,16 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
     QS_CUDA(s, cudaMallocAsync(&ws, need, s->stream));
     own = true;
   }
+  // frees the frames on every early return; the normal path frees them itself
+  // and checks the result
+  struct FramesGuard {
+    qs_sim *s;
+    void *ws;
+    bool own;
+    ~FramesGuard() {
+      if (own && cudaFreeAsync(ws, s->stream) != cudaSuccess) cudaGetLastError();
+    }
+  } guard{s, ws, own};
   Carve c;
   uint8_t *b = static_cast<uint8_t *>(ws);
   const uint32_t n = s->d.L.n;
@@ -773,6 +786,7 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
   }
   if (!out_dev && M)
     QS_CUDA(s, cudaMemcpyAsync(record, dout, (size_t)(M * ow * 8), cudaMemcpyDeviceToHost, s->stream));
+  guard.own = false;
   if (own) QS_CUDA(s, cudaFreeAsync(ws, s->stream));
   if (!out_dev) return qs_sim_sync(s);
   return QS_OK;

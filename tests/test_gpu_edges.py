@@ -62,3 +62,27 @@ def test_batch_with_empty_and_measure_only_circuits():
         _, orec, _ = O.run_circuit(c, seed=seeds[i])
         assert np.array_equal(b.record(i), orec), i
     assert not b.record(2).any()  # |0...0>: every outcome is 0
+
+
+def test_host_checks_reject_bad_ranges_and_keep_the_sim_usable():
+    """Ranges that would wrap around 64 bits and negative layer offsets are
+    refused on the host before any device access; the sim stays usable."""
+    import ctypes
+    L = qs.lib()
+    circ = C.random_circuit(70, 5, 0.5, seed=11, final_measure_all=True)
+    sim = qs.Simulator(70, device="cuda:0")
+    rec = sim.run(circ, seed=5)
+    buf = np.zeros(8, np.uint8)
+    p = ctypes.c_void_p(buf.ctypes.data)
+    h = ctypes.c_void_p(sim.sim)
+    assert L.qs_sim_record(h, 2**64 - 1, 2, p) == -1
+    assert L.qs_sim_record_kinds(h, 3, 2**64 - 2, p) == -1
+    assert L.qs_sim_record(h, len(rec), 1, p) == -1
+    dc = sim.upload(circ)
+    bad = np.array([-2, 0], np.int64)
+    assert L.qs_sim_apply_layers_dev(h, ctypes.c_void_p(dc.packed.data_ptr()),
+                                     ctypes.c_void_p(bad.ctypes.data), 0, 1) == -1
+    sim.sync()
+    _, orec, _ = O.run_circuit(circ, seed=5)
+    assert np.array_equal(sim.record(), orec)
+    assert np.array_equal(sim.record(len(rec) - 3, 3), orec[-3:])
