@@ -84,19 +84,27 @@ typedef struct qs_options {
  * two launches per measurement; results are identical either way. */
 #define QS_FLAG_UNPIPELINED_MEASURE 2u
 /* qs_options.flags: never measure in blocks. By default a window of >= 16
- * measurements on >= 1024 qubits is measured in blocks of up to 64 with one
+ * measurements on >= 64 qubits is measured in blocks of up to 64 with one
  * pass over the tableau per block (identical results); the blocked path waits
  * for the stream once per block. */
 #define QS_FLAG_NO_BLOCKED_MEASURE 4u
 
 typedef struct qs_sim qs_sim;
 
-/* Layouts for qs_sim_tableau_export. */
+/* Layouts for qs_sim_tableau_export and qs_sim_tableau_import. */
 enum {
-  /* Host rows 0..2n-1 (destabilizers, then stabilizers), each ceil(n/64)
+  /* Rows 0..2n-1 (destabilizers, then stabilizers), each ceil(n/64)
    * x-words then ceil(n/64) z-words (bit j of word w = qubit 64 w + j),
    * followed by ceil(2n/64) sign words (bit i = sign of row i). */
-  QS_LAYOUT_ROWS_PACKED = 0
+  QS_LAYOUT_ROWS_PACKED = 0,
+  /* The device's own column-major layout (the one gate layers run on, Sec. 4.1),
+   * copied without repacking. With k = ceil(n/64) and W = 4 ceil(k/2) (2k
+   * rounded up to a multiple of 4): n X columns of W words (column of qubit q
+   * at word q W), then n Z columns of W words, then W sign words. Bit g of a
+   * column or of the sign words belongs to generator g in packed numbering:
+   * destabilizer i at g = i, stabilizer i at g = 64 k + i; every other bit is
+   * zero. (2n + 1) W words in all. */
+  QS_LAYOUT_NATIVE = 1
 };
 
 /* Library version string. */
@@ -257,22 +265,26 @@ int qs_sim_sample(qs_sim *sim, uint64_t shots, uint64_t seed, uint64_t *record,
                   size_t record_words, void *frame_ws, size_t frame_ws_bytes);
 
 /*
- * Copies the tableau out in `layout` (QS_LAYOUT_ROWS_PACKED) to host memory.
- * needed: if not NULL, receives the byte size. dst may be NULL to query.
- * Errors: QS_ERR_SIZE when dst_bytes is too small. Syncs.
+ * Copies the tableau out in `layout` (QS_LAYOUT_ROWS_PACKED or
+ * QS_LAYOUT_NATIVE) to host or device memory (told apart by unified
+ * addressing). needed: if not NULL, receives the byte size. dst may be NULL
+ * to query. NATIVE needs no repacking on the host, only the layout switch
+ * back to columns when the last operation was a measurement.
+ * Errors: QS_ERR_ARG (unknown layout), QS_ERR_SIZE (dst_bytes too small). Syncs.
  */
 int qs_sim_tableau_export(qs_sim *sim, int layout, void *dst, size_t dst_bytes, size_t *needed);
 
 /*
  * Restores a checkpoint (the paper has none; tableau, record and keys make one
  * because the coins are keyed by record index): the tableau from a host
- * buffer in qs_sim_tableau_export's layout and the first record_count record
- * entries (0/1 bytes, host). Measurements after the import continue the
+ * buffer in one of qs_sim_tableau_export's layouts and the first
+ * record_count record entries (0/1 bytes, host). Measurements after the import continue the
  * record at index record_count, so with the same keys they reproduce the
  * uninterrupted run bit for bit. The op log is cleared and qs_sim_sample is
  * refused (QS_ERR_STATE) until qs_sim_reset: frame sampling replays the
- * program from |0...0>. The tableau is not checked for validity beyond zero
- * bits past qubit n - 1 (QS_ERR_ARG). Syncs.
+ * program from |0...0>. The tableau is not checked for validity beyond its
+ * padding bits (past qubit n - 1 in ROWS_PACKED, outside the packed generator
+ * numbering in NATIVE), which must be zero (QS_ERR_ARG). Syncs.
  * Errors: QS_ERR_ARG (layout, padding bits, NULL record), QS_ERR_SIZE
  * (src_bytes too small, record_count above the record capacity).
  */

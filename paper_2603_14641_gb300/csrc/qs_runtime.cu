@@ -16,6 +16,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -792,38 +793,69 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
   return QS_OK;
 }
 
+static size_t tableau_bytes(const Layout &L, int layout) {
+  if (layout == QS_LAYOUT_NATIVE) return (2ull * L.n + 1) * L.cs * 8;
+  return (2ull * L.n * 2 * L.k + (2ull * L.n + 63) / 64) * 8;
+}
+
 int qs_sim_tableau_export(qs_sim *s, int layout, void *dst, size_t dst_bytes, size_t *needed) {
   Range range_("qs_sim_tableau_export");
   int rc = check_usable(s);
   if (rc) return rc;
-  if (layout != QS_LAYOUT_ROWS_PACKED) return fail(QS_ERR_ARG, "unknown layout");
+  if (layout != QS_LAYOUT_ROWS_PACKED && layout != QS_LAYOUT_NATIVE)
+    return fail(QS_ERR_ARG, "unknown layout");
   const Layout &L = s->d.L;
   const uint32_t n = L.n, k = L.k;
-  const size_t sw = (2ull * n + 63) / 64;
-  const size_t bytes = (2ull * n * 2 * k + sw) * 8;
+  const size_t bytes = tableau_bytes(L, layout);
   if (needed) *needed = bytes;
   if (!dst) return QS_OK;
   if (dst_bytes < bytes) return fail(QS_ERR_SIZE, "export buffer too small");
-  if ((rc = ensure_rows(s))) return rc;
   uint64_t *o = static_cast<uint64_t *>(dst);
+  // cudaMemcpyDefault: dst may be host or device memory
+  if (layout == QS_LAYOUT_NATIVE) {
+    if ((rc = ensure_cols(s))) return rc;
+    const size_t colw = (size_t)n * L.cs;
+    QS_CUDA(s, cudaMemcpyAsync(o, s->d.X, colw * 8, cudaMemcpyDefault, s->stream));
+    QS_CUDA(s, cudaMemcpyAsync(o + colw, s->d.Z, colw * 8, cudaMemcpyDefault, s->stream));
+    QS_CUDA(s, cudaMemcpyAsync(o + 2 * colw, s->d.S, (size_t)L.cs * 8, cudaMemcpyDefault, s->stream));
+    return qs_sim_sync(s);
+  }
+  if ((rc = ensure_rows(s))) return rc;
   const size_t dp = 2ull * k * 8, sp = (size_t)L.rs * 8, wb = (size_t)k * 8;
-  QS_CUDA(s, cudaMemcpy2DAsync(o, dp, s->d.RX, sp, wb, n, cudaMemcpyDeviceToHost, s->stream));
-  QS_CUDA(s, cudaMemcpy2DAsync(o + k, dp, s->d.RZ, sp, wb, n, cudaMemcpyDeviceToHost, s->stream));
+  QS_CUDA(s, cudaMemcpy2DAsync(o, dp, s->d.RX, sp, wb, n, cudaMemcpyDefault, s->stream));
+  QS_CUDA(s, cudaMemcpy2DAsync(o + k, dp, s->d.RZ, sp, wb, n, cudaMemcpyDefault, s->stream));
   const size_t st = 64ull * k * L.rs;
-  QS_CUDA(s, cudaMemcpy2DAsync(o + (size_t)n * 2 * k, dp, s->d.RX + st, sp, wb, n,
-                               cudaMemcpyDeviceToHost, s->stream));
+  QS_CUDA(s, cudaMemcpy2DAsync(o + (size_t)n * 2 * k, dp, s->d.RX + st, sp, wb, n, cudaMemcpyDefault,
+                               s->stream));
   QS_CUDA(s, cudaMemcpy2DAsync(o + (size_t)n * 2 * k + k, dp, s->d.RZ + st, sp, wb, n,
-                               cudaMemcpyDeviceToHost, s->stream));
+                               cudaMemcpyDefault, s->stream));
   std::vector<uint64_t> S(L.cs);
   QS_CUDA(s, cudaMemcpyAsync(S.data(), s->d.S, (size_t)L.cs * 8, cudaMemcpyDeviceToHost, s->stream));
   if ((rc = qs_sim_sync(s))) return rc;
-  uint64_t *sig = o + 2ull * n * 2 * k;
-  for (size_t w = 0; w < sw; ++w) sig[w] = 0;
+  const size_t sw = (2ull * n + 63) / 64;
+  std::vector<uint64_t> sig(sw, 0);
   for (uint64_t i = 0; i < 2ull * n; ++i) {
     const uint64_t pr = i < n ? i : 64ull * k + (i - n);
     if ((S[pr >> 6] >> (pr & 63)) & 1u) sig[i >> 6] |= 1ull << (i & 63);
   }
+  QS_CUDA(s, cudaMemcpy(o + 2ull * n * 2 * k, sig.data(), sw * 8, cudaMemcpyDefault));
   return QS_OK;
+}
+
+// Words of a W-word NATIVE vector that hold bits belonging to no generator
+// (packed numbers [n, 64 k) and [64 k + n, 64 W)), with those bits' mask.
+static std::vector<std::pair<uint32_t, uint64_t>> native_padding(const Layout &L) {
+  const uint64_t n = L.n, k = L.k;
+  std::vector<std::pair<uint32_t, uint64_t>> pads;
+  for (uint64_t w = 0; w < L.cs; ++w) {
+    uint64_t pad = 0;
+    for (int b = 0; b < 64; ++b) {
+      const uint64_t g = 64 * w + b;
+      if (!(g < n || (g >= 64 * k && g < 64 * k + n))) pad |= 1ull << b;
+    }
+    if (pad) pads.emplace_back((uint32_t)w, pad);
+  }
+  return pads;
 }
 
 int qs_sim_tableau_import(qs_sim *s, int layout, const void *src, size_t src_bytes,
@@ -831,41 +863,60 @@ int qs_sim_tableau_import(qs_sim *s, int layout, const void *src, size_t src_byt
   Range range_("qs_sim_tableau_import");
   int rc = check_usable(s);
   if (rc) return rc;
-  if (layout != QS_LAYOUT_ROWS_PACKED) return fail(QS_ERR_ARG, "unknown layout");
+  if (layout != QS_LAYOUT_ROWS_PACKED && layout != QS_LAYOUT_NATIVE)
+    return fail(QS_ERR_ARG, "unknown layout");
   const Layout &L = s->d.L;
   const uint32_t n = L.n, k = L.k;
-  const size_t sw = (2ull * n + 63) / 64;
-  const size_t bytes = (2ull * n * 2 * k + sw) * 8;
+  const size_t bytes = tableau_bytes(L, layout);
   if (!src || src_bytes < bytes) return fail(QS_ERR_SIZE, "import buffer smaller than the tableau");
   if (record_count > s->d.record_cap)
     return fail(QS_ERR_SIZE, "record capacity exceeded (qs_options.record_capacity)");
   if (record_count && !record) return fail(QS_ERR_ARG, "record is NULL");
   const uint64_t *in = static_cast<const uint64_t *>(src);
-  // bits of qubits >= n in the last word of each row must be zero
-  if (n & 63) {
-    const uint64_t pad = ~0ull << (n & 63);
-    for (uint64_t i = 0; i < 2ull * n; ++i)
-      if ((in[i * 2 * k + k - 1] | in[i * 2 * k + 2 * k - 1]) & pad)
-        return fail(QS_ERR_ARG, "row " + std::to_string(i) + " has bits beyond qubit n - 1");
+  if (layout == QS_LAYOUT_NATIVE) {
+    const auto pads = native_padding(L);
+    for (uint64_t c = 0; c < 2ull * n + 1; ++c)  // n X columns, n Z columns, the signs
+      for (const auto &pw : pads)
+        if (in[c * L.cs + pw.first] & pw.second)
+          return fail(QS_ERR_ARG, "vector " + std::to_string(c) + " has bits outside the generators "
+                                  "(word " + std::to_string(pw.first) + ")");
+    const size_t colw = (size_t)n * L.cs;
+    const size_t allw = (size_t)L.ncols * L.cs;  // padding qubit columns stay zero
+    QS_CUDA(s, cudaMemsetAsync(s->d.X, 0, allw * 8, s->stream));
+    QS_CUDA(s, cudaMemsetAsync(s->d.Z, 0, allw * 8, s->stream));
+    QS_CUDA(s, cudaMemcpyAsync(s->d.X, in, colw * 8, cudaMemcpyHostToDevice, s->stream));
+    QS_CUDA(s, cudaMemcpyAsync(s->d.Z, in + colw, colw * 8, cudaMemcpyHostToDevice, s->stream));
+    QS_CUDA(s, cudaMemcpyAsync(s->d.S, in + 2 * colw, (size_t)L.cs * 8, cudaMemcpyHostToDevice,
+                               s->stream));
+  } else {
+    // bits of qubits >= n in the last word of each row must be zero
+    if (n & 63) {
+      const uint64_t pad = ~0ull << (n & 63);
+      for (uint64_t i = 0; i < 2ull * n; ++i)
+        if ((in[i * 2 * k + k - 1] | in[i * 2 * k + 2 * k - 1]) & pad)
+          return fail(QS_ERR_ARG, "row " + std::to_string(i) + " has bits beyond qubit n - 1");
+    }
+    const uint64_t *sig = in + 2ull * n * 2 * k;
+    std::vector<uint64_t> S(L.cs, 0);
+    for (uint64_t i = 0; i < 2ull * n; ++i) {
+      const uint64_t pr = i < n ? i : 64ull * k + (i - n);
+      if ((sig[i >> 6] >> (i & 63)) & 1u) S[pr >> 6] |= 1ull << (pr & 63);
+    }
+    const size_t rowb = (size_t)L.nrows * L.rs * 8;
+    QS_CUDA(s, cudaMemsetAsync(s->d.RX, 0, rowb, s->stream));
+    QS_CUDA(s, cudaMemsetAsync(s->d.RZ, 0, rowb, s->stream));
+    const size_t sp = 2ull * k * 8, dp = (size_t)L.rs * 8, wb = (size_t)k * 8;
+    const size_t st = 64ull * k * L.rs;
+    QS_CUDA(s, cudaMemcpy2DAsync(s->d.RX, dp, in, sp, wb, n, cudaMemcpyHostToDevice, s->stream));
+    QS_CUDA(s, cudaMemcpy2DAsync(s->d.RZ, dp, in + k, sp, wb, n, cudaMemcpyHostToDevice, s->stream));
+    QS_CUDA(s, cudaMemcpy2DAsync(s->d.RX + st, dp, in + (size_t)n * 2 * k, sp, wb, n,
+                                 cudaMemcpyHostToDevice, s->stream));
+    QS_CUDA(s, cudaMemcpy2DAsync(s->d.RZ + st, dp, in + (size_t)n * 2 * k + k, sp, wb, n,
+                                 cudaMemcpyHostToDevice, s->stream));
+    QS_CUDA(s, cudaMemcpyAsync(s->d.S, S.data(), (size_t)L.cs * 8, cudaMemcpyHostToDevice, s->stream));
+    // the host vector must outlive the copy
+    QS_CUDA(s, cudaStreamSynchronize(s->stream));
   }
-  const uint64_t *sig = in + 2ull * n * 2 * k;
-  std::vector<uint64_t> S(L.cs, 0);
-  for (uint64_t i = 0; i < 2ull * n; ++i) {
-    const uint64_t pr = i < n ? i : 64ull * k + (i - n);
-    if ((sig[i >> 6] >> (i & 63)) & 1u) S[pr >> 6] |= 1ull << (pr & 63);
-  }
-  const size_t rowb = (size_t)L.nrows * L.rs * 8;
-  QS_CUDA(s, cudaMemsetAsync(s->d.RX, 0, rowb, s->stream));
-  QS_CUDA(s, cudaMemsetAsync(s->d.RZ, 0, rowb, s->stream));
-  const size_t sp = 2ull * k * 8, dp = (size_t)L.rs * 8, wb = (size_t)k * 8;
-  const size_t st = 64ull * k * L.rs;
-  QS_CUDA(s, cudaMemcpy2DAsync(s->d.RX, dp, in, sp, wb, n, cudaMemcpyHostToDevice, s->stream));
-  QS_CUDA(s, cudaMemcpy2DAsync(s->d.RZ, dp, in + k, sp, wb, n, cudaMemcpyHostToDevice, s->stream));
-  QS_CUDA(s, cudaMemcpy2DAsync(s->d.RX + st, dp, in + (size_t)n * 2 * k, sp, wb, n,
-                               cudaMemcpyHostToDevice, s->stream));
-  QS_CUDA(s, cudaMemcpy2DAsync(s->d.RZ + st, dp, in + (size_t)n * 2 * k + k, sp, wb, n,
-                               cudaMemcpyHostToDevice, s->stream));
-  QS_CUDA(s, cudaMemcpyAsync(s->d.S, S.data(), (size_t)L.cs * 8, cudaMemcpyHostToDevice, s->stream));
   if (record_count) {
     QS_CUDA(s, cudaMemcpyAsync(s->d.record, record, record_count, cudaMemcpyHostToDevice, s->stream));
     QS_CUDA(s, cudaMemsetAsync(s->d.kinds, 2, record_count, s->stream));
@@ -874,8 +925,8 @@ int qs_sim_tableau_import(qs_sim *s, int layout, const void *src, size_t src_byt
   QS_CUDA(s, launch_reset_meas_state(s->d, s->stream));
   s->launches += 1;
   QS_CUDA(s, cudaStreamSynchronize(s->stream));  // the host buffers may go once this returns
-  s->rows_valid = true;
-  s->cols_valid = false;
+  s->rows_valid = layout == QS_LAYOUT_ROWS_PACKED;
+  s->cols_valid = layout == QS_LAYOUT_NATIVE;
   s->n_meas = record_count;
   s->n_noise = 0;
   s->ops.clear();

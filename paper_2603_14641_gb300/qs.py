@@ -21,6 +21,7 @@ QS_OK = 0
 ERRORS = {-1: "QS_ERR_ARG", -2: "QS_ERR_OOM", -3: "QS_ERR_CUDA", -4: "QS_ERR_TIMEOUT",
           -5: "QS_ERR_SIZE", -6: "QS_ERR_STATE", -7: "QS_ERR_INTERNAL"}
 QS_LAYOUT_ROWS_PACKED = 0
+QS_LAYOUT_NATIVE = 1
 
 GATES = dict(I=0, X=1, Y=2, Z=3, H=4, S=5, SDG=6, CX=7, CY=8, CZ=9, SWAP=10, ISWAP=11)
 QS_MEASURE = 12
@@ -217,12 +218,13 @@ def qs_sim_measure_dev(sim: int, qubits_dev: int, count: int, seed: int, shot: i
                                     qs_key(seed, shot)), "qs_sim_measure_dev")
 
 
-def qs_sim_tableau_import(sim: int, packed: np.ndarray, record: np.ndarray) -> None:
-    """Restores a checkpoint: `packed` as returned by qs_sim_tableau_export,
-    `record` the 0/1 record bytes so far."""
+def qs_sim_tableau_import(sim: int, packed: np.ndarray, record: np.ndarray,
+                          layout: int = QS_LAYOUT_ROWS_PACKED) -> None:
+    """Restores a checkpoint: `packed` as returned by qs_sim_tableau_export in
+    `layout`, `record` the 0/1 record bytes so far."""
     t = np.ascontiguousarray(packed, np.uint64)
     r = np.ascontiguousarray(record, np.uint8)
-    _check(lib().qs_sim_tableau_import(ctypes.c_void_p(sim), QS_LAYOUT_ROWS_PACKED,
+    _check(lib().qs_sim_tableau_import(ctypes.c_void_p(sim), int(layout),
                                        t.ctypes.data, t.nbytes, r.ctypes.data if len(r) else None,
                                        len(r)), "qs_sim_tableau_import")
 
@@ -274,14 +276,22 @@ def qs_sim_sample_noalloc(sim: int, shots: int, seed: int, record: int, record_w
            "qs_sim_sample_noalloc")
 
 
-def qs_sim_tableau_export(sim: int) -> np.ndarray:
+def qs_sim_tableau_export(sim: int, layout: int = QS_LAYOUT_ROWS_PACKED, out=None):
+    """The tableau in `layout` as uint64 words: into `out` (a numpy array or a
+    torch tensor, host or device, of at least the needed bytes) if given, else
+    into a new numpy array."""
     need = ctypes.c_size_t(0)
-    _check(lib().qs_sim_tableau_export(ctypes.c_void_p(sim), QS_LAYOUT_ROWS_PACKED, None, 0,
+    _check(lib().qs_sim_tableau_export(ctypes.c_void_p(sim), int(layout), None, 0,
                                        ctypes.byref(need)), "qs_sim_tableau_export")
-    buf = np.zeros(need.value // 8, np.uint64)
-    _check(lib().qs_sim_tableau_export(ctypes.c_void_p(sim), QS_LAYOUT_ROWS_PACKED, _ptr(buf),
-                                       need.value, None), "qs_sim_tableau_export")
-    return buf
+    if out is None:
+        out = np.zeros(need.value // 8, np.uint64)
+    if isinstance(out, np.ndarray):
+        ptr, nbytes = out.ctypes.data, out.nbytes
+    else:
+        ptr, nbytes = out.data_ptr(), out.numel() * out.element_size()
+    _check(lib().qs_sim_tableau_export(ctypes.c_void_p(sim), int(layout), ctypes.c_void_p(ptr),
+                                       nbytes, None), "qs_sim_tableau_export")
+    return out
 
 
 def qs_sim_export_rows(sim: int, rows: np.ndarray, n: int):
@@ -318,6 +328,19 @@ def unpack_rows(buf: np.ndarray, n: int):
     sw = (2 * n + 63) // 64
     sig = np.unpackbits(buf[2 * n * 2 * k:2 * n * 2 * k + sw].view(np.uint8), bitorder="little")
     return np.ascontiguousarray(x), np.ascontiguousarray(z), np.ascontiguousarray(sig[:2 * n])
+
+
+def unpack_native(buf: np.ndarray, n: int):
+    """NATIVE export -> (x, z, r) uint8 arrays of shapes (2n, n), (2n, n), (2n,)
+    in generator order (destabilizers, then stabilizers)."""
+    k = (n + 63) // 64
+    W = (2 * k + 3) // 4 * 4
+    cols = np.ascontiguousarray(buf[:(2 * n + 1) * W]).reshape(2 * n + 1, W)
+    bits = np.unpackbits(cols.view(np.uint8), axis=1, bitorder="little")  # (2n + 1, 64 W)
+    gen = np.concatenate([np.arange(n), 64 * k + np.arange(n)])  # packed number of generator i
+    x = bits[:n, gen].T
+    z = bits[n:2 * n, gen].T
+    return np.ascontiguousarray(x), np.ascontiguousarray(z), np.ascontiguousarray(bits[2 * n, gen])
 
 
 # ----------------------------------------------------------------------
@@ -381,12 +404,12 @@ class Simulator:
         self._keep.append(qubits_dev)
         qs_sim_measure_dev(self.sim, qubits_dev.data_ptr(), qubits_dev.numel(), seed, shot)
 
-    def checkpoint(self):
+    def checkpoint(self, layout: int = QS_LAYOUT_ROWS_PACKED):
         """(packed tableau, record): everything a later run needs to resume."""
-        return qs_sim_tableau_export(self.sim), self.record()
+        return qs_sim_tableau_export(self.sim, layout), self.record()
 
-    def restore(self, packed, record):
-        qs_sim_tableau_import(self.sim, packed, record)
+    def restore(self, packed, record, layout: int = QS_LAYOUT_ROWS_PACKED):
+        qs_sim_tableau_import(self.sim, packed, record, layout)
 
     def noise(self, kind: int, p: float, targets):
         """Appends a Pauli noise channel (QS_NOISE_*) for the sampled shots."""

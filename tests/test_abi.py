@@ -102,3 +102,31 @@ def test_create_without_device_fails_loudly():
         pass
     with pytest.raises(qs.QsError):
         qs.qs_sim_create(64)
+
+
+def test_layout_codes_and_native_unpacking():
+    """The layout codes agree with the header, and unpack_native reads a NATIVE
+    buffer written here bit by bit from its documented definition."""
+    text = open(HEADER).read()
+    for name in ["QS_LAYOUT_ROWS_PACKED", "QS_LAYOUT_NATIVE"]:
+        m = re.search(rf"{name}\s*=\s*(\d+)", text)
+        assert m and int(m.group(1)) == getattr(qs, name)
+    rng = np.random.default_rng(4)
+    for n in (1, 63, 64, 65, 130, 300):
+        x = rng.integers(0, 2, (2 * n, n), dtype=np.uint8)
+        z = rng.integers(0, 2, (2 * n, n), dtype=np.uint8)
+        r = rng.integers(0, 2, 2 * n, dtype=np.uint8)
+        k = -(-n // 64)
+        W = 4 * -(-k // 2)
+        buf = np.zeros((2 * n + 1) * W, np.uint64)
+        for i in range(2 * n):
+            g = i if i < n else 64 * k + (i - n)
+            w, b = divmod(g, 64)
+            for q in np.nonzero(x[i])[0]:
+                buf[q * W + w] |= np.uint64(1) << np.uint64(b)
+            for q in np.nonzero(z[i])[0]:
+                buf[(n + q) * W + w] |= np.uint64(1) << np.uint64(b)
+            if r[i]:
+                buf[2 * n * W + w] |= np.uint64(1) << np.uint64(b)
+        ux, uz, ur = qs.unpack_native(buf, n)
+        assert np.array_equal(ux, x) and np.array_equal(uz, z) and np.array_equal(ur, r)

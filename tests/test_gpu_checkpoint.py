@@ -110,3 +110,42 @@ def test_bad_checkpoints_are_rejected():
     with pytest.raises(qs.QsError) as e:
         sim.restore(packed[:-1], rec)
     assert e.value.code == -5
+
+
+@pytest.mark.parametrize("n", [70, 1500])
+def test_native_layout_export_import_and_device_destination(n):
+    """NATIVE export decodes to the oracle's tableau; exports into device memory
+    equal the host ones; a NATIVE checkpoint resumes bit for bit; padding bits
+    in a NATIVE checkpoint are rejected."""
+    circ = C.random_circuit(n, 16, 0.5, seed=n + 1, measure_every=4, measure_frac=0.2,
+                            final_measure_all=True)
+    half = len(circ.ops) // 2
+    a = qs.Simulator(n, device="cuda:0")
+    _run_ops(a, circ, circ.ops[:half], seed=5)  # ends after a measurement window or a layer
+    native, rec = a.checkpoint(qs.QS_LAYOUT_NATIVE)
+    # the oracle's state at the checkpoint: the same circuit cut after the same ops
+    trunc = C.Circuit(n=n, gates=circ.gates, layer_ptr=circ.layer_ptr, ops=list(circ.ops[:half]))
+    ot, orec, _ = O.run_circuit(trunc, seed=5)
+    assert np.array_equal(rec, orec)
+    for u, v in zip(qs.unpack_native(native, n), ot.get()):
+        assert np.array_equal(u, v)
+    rows = qs.qs_sim_tableau_export(a.sim)
+    for fmt, host in [(qs.QS_LAYOUT_NATIVE, native), (qs.QS_LAYOUT_ROWS_PACKED, rows)]:
+        dev = torch.zeros(len(host), dtype=torch.int64, device="cuda:0")
+        qs.qs_sim_tableau_export(a.sim, fmt, out=dev)
+        assert np.array_equal(dev.cpu().numpy().view(np.uint64), host)
+    _run_ops(a, circ, circ.ops[half:], seed=5)
+    b = qs.Simulator(n, device="cuda:0")
+    b.restore(native, rec, qs.QS_LAYOUT_NATIVE)
+    _run_ops(b, circ, circ.ops[half:], seed=5)
+    assert np.array_equal(a.record(), b.record())
+    for u, v in zip(a.export(), b.export()):
+        assert np.array_equal(u, v)
+    k = (n + 63) // 64
+    W = (2 * k + 3) // 4 * 4
+    bad = native.copy()
+    bad[3 * W + k - 1] |= np.uint64(1) << np.uint64(63)  # destabilizer number 64 k - 1 >= n
+    c = qs.Simulator(n, device="cuda:0")
+    with pytest.raises(qs.QsError) as e:
+        c.restore(bad, rec, qs.QS_LAYOUT_NATIVE)
+    assert e.value.code == -1
