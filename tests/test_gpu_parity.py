@@ -282,6 +282,28 @@ def test_full_180k_measure_twice_and_inverse():
     sim2.sync()
 
 
+@pytest.mark.slow
+def test_oracle_parity_on_a_20k_prefix_of_the_180k_workload():
+    """The 180,000-qubit workload's generator (p_cx 0.4, seed 3) at 20,000
+    qubits: its first two layers, then the first 64 of the final all-qubit
+    measurement (blocked, with deterministic steps in between), against the
+    oracle: record, kinds and the whole tableau."""
+    n = 20_000
+    circ = C.workload_180k_prefix(n, depth=2)
+    q = np.arange(64, dtype=np.uint32)
+    prog = C.Circuit(n=n, gates=circ.gates, layer_ptr=circ.layer_ptr,
+                     ops=[("layers", 0, 2), ("measure", q)])
+    sim = _sim(n)
+    dc = sim.upload(prog)
+    rec = sim.run(prog, seed=7, dc=dc)
+    o, orec, okinds = O.run_circuit(prog, seed=7)
+    assert 0 < int(okinds.sum()) < len(q)  # both kinds occur
+    assert np.array_equal(rec, orec)
+    assert np.array_equal(sim.record_kinds(), okinds)
+    _assert_tableau(sim, o)
+    sim.sync()
+
+
 @pytest.mark.parametrize("n", [1, 64, 65, 300, 2000, 14080, 14081])
 def test_fused_segments_match_per_layer_kernels(n):
     """Device-resident layers run through the fused shared-memory kernel when
