@@ -364,9 +364,10 @@ def test_pipelined_measurements_match_five_launch_path(n):
         assert np.array_equal(outs[0][0], orec)
 
 
-@pytest.mark.parametrize("n,count", [(1024, 16), (1100, 200), (2000, 150), (4097, 70)])
+@pytest.mark.parametrize("n,count", [(64, 16), (65, 64), (256, 256), (300, 100), (1024, 16),
+                                     (1100, 200), (2000, 150), (4097, 70)])
 def test_blocked_measurement_matches_oracle(n, count):
-    """Windows of >= 16 measurements on >= 1024 qubits go through the blocked
+    """Windows of >= 16 measurements on >= 64 qubits go through the blocked
     path (up to 64 measurements per tableau pass); repeated qubits force
     deterministic outcomes that end a block early."""
     circ = C.random_circuit(n, 12, 0.5, seed=n + count, final_measure_all=False)
