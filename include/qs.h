@@ -88,6 +88,12 @@ typedef struct qs_options {
  * pass over the tableau per block (identical results); the blocked path waits
  * for the stream once per block. */
 #define QS_FLAG_NO_BLOCKED_MEASURE 4u
+/* qs_options.flags: address the row-major tableau with 64-bit word offsets in
+ * the blocked measurement's apply pass even when 32-bit ones suffice. By
+ * default 64-bit offsets are used only when the row-major matrix holds 2^32
+ * words or more (about 371,000 qubits and up); the flag runs that code path on
+ * a tableau of any size (identical results). */
+#define QS_FLAG_WIDE_OFFSETS 8u
 
 typedef struct qs_sim qs_sim;
 

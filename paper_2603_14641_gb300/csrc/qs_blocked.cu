@@ -677,7 +677,7 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   // small next to the rows it serves
   const uint32_t rows_y = std::max<uint32_t>(
       1, (uint32_t)std::min<uint64_t>(((uint64_t)d.sms * 8 + chunks - 1) / chunks, L.nrows / 512));
-  if ((uint64_t)L.nrows * L.rs < (1ull << 32))
+  if (!d.wide_offsets && (uint64_t)L.nrows * L.rs < (1ull << 32))
     blk_apply_kernel<uint32_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
         d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, M, base, Tp, st);
   else

@@ -118,6 +118,7 @@ struct Dev {
   uint8_t *kinds;          // per record entry: 1 probabilistic, 0 deterministic, 2 restored
   uint64_t record_cap;
   int sms;                 // multiprocessor count of the device
+  bool wide_offsets;       // 64-bit row offsets in the blocked apply pass at any size
 };
 
 cudaError_t launch_init(const Dev &d, const uint8_t *initstate_dev, cudaStream_t s);

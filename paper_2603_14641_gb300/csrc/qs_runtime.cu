@@ -278,6 +278,7 @@ int qs_sim_create(uint32_t n, const qs_options *opt, void *cuda_stream, void *wo
   s->plan = make_plan(s->d.L, opt);
   s->stream = static_cast<cudaStream_t>(cuda_stream);
   s->flags = opt ? opt->flags : 0u;
+  s->d.wide_offsets = (s->flags & QS_FLAG_WIDE_OFFSETS) != 0;
   if (workspace) {
     if (workspace_bytes < s->plan.total) {
       delete s;

@@ -151,6 +151,7 @@ def qs_version() -> str:
 QS_FLAG_NO_FUSION = 1
 QS_FLAG_UNPIPELINED_MEASURE = 2
 QS_FLAG_NO_BLOCKED_MEASURE = 4
+QS_FLAG_WIDE_OFFSETS = 8
 
 
 def qs_sim_required_bytes(n: int, record_capacity: int = 0) -> int:

@@ -130,3 +130,11 @@ def test_layout_codes_and_native_unpacking():
                 buf[2 * n * W + w] |= np.uint64(1) << np.uint64(b)
         ux, uz, ur = qs.unpack_native(buf, n)
         assert np.array_equal(ux, x) and np.array_equal(uz, z) and np.array_equal(ur, r)
+
+
+def test_option_flags_match_header():
+    text = open(HEADER).read()
+    for name in ["QS_FLAG_NO_FUSION", "QS_FLAG_UNPIPELINED_MEASURE", "QS_FLAG_NO_BLOCKED_MEASURE",
+                 "QS_FLAG_WIDE_OFFSETS"]:
+        m = re.search(rf"#define\s+{name}\s+(\d+)u", text)
+        assert m and int(m.group(1)) == getattr(qs, name), name

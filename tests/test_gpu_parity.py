@@ -387,6 +387,27 @@ def test_blocked_measurement_matches_oracle(n, count):
     sim.sync()
 
 
+@pytest.mark.parametrize("n,count", [(300, 100), (4097, 150)])
+def test_wide_offset_apply_pass_matches_oracle(n, count):
+    """The blocked apply pass with 64-bit row offsets (the code path of
+    tableaus of 2^32 words and more, forced by QS_FLAG_WIDE_OFFSETS) against
+    the oracle and the default 32-bit path."""
+    circ = C.random_circuit(n, 10, 0.5, seed=n + 3, final_measure_all=False)
+    rng = np.random.default_rng(n)
+    q = rng.permutation(n)[:count].astype(np.uint32)
+    q = np.concatenate([q[: count // 2], q[: 5], q[count // 2:]])
+    o = O.Oracle(n)
+    o.apply(circ.gates)
+    orec, _ = o.measure(q, seed=6)
+    for flags in (qs.QS_FLAG_WIDE_OFFSETS, 0):
+        sim = _sim(n, flags=flags)
+        dc = sim.upload(circ)
+        sim.apply_layers_dev(dc, 0, circ.n_layers)
+        assert np.array_equal(sim.measure(q, seed=6), orec)
+        _assert_tableau(sim, o)
+        sim.sync()
+
+
 @pytest.mark.parametrize("n", [1500, 40000])
 def test_blocked_matches_unblocked(n):
     depth = 8
