@@ -260,6 +260,7 @@ size_t qs_sim_sample_required_bytes(const qs_sim *sim, uint64_t shots);
  * Frame words: word j (shots 64 j .. 64 j + 63) of qubit q after event e is
  * word (j & 3) of Philox(counter = (e, q, j >> 2, 1), key = (seed, 0xF4A3E)),
  * e = 0 at initialisation and e = m + 1 after measurement m.
+ *   shots:  1 .. 2e9 (QS_ERR_ARG otherwise).
  *   record: [M][ceil(shots/64)] uint64 (M = qs_sim_num_measurements), bit s of
  *           word j of measurement m = outcome of shot 64 j + s (bits >= shots
  *           are 0); host or device pointer; record_words >= M * ceil(shots/64).

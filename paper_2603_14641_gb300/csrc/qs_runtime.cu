@@ -57,6 +57,9 @@ constexpr int kRing = 4;
 constexpr uint32_t kBlockedMinCount = 16;    // windows this long use blocked measurement
 constexpr uint32_t kBlockedMinQubits = 64;
 constexpr uint32_t kMaxQubits = 1u << 20;
+// Frame layers cover a qubit's shot words in chunks of 512 words along grid.y
+// (at most 65,535): 2e9 shots are 31.25 M words, 61,036 chunks.
+constexpr uint64_t kMaxShots = 2000000000ull;
 
 struct Carve {
   size_t off = 0;
@@ -695,10 +698,9 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
   if (s->resumed)
     return fail(QS_ERR_STATE, "sampling replays the op log from |0...0>; a sim restored by "
                               "qs_sim_tableau_import has none (qs_sim_reset first)");
-  if (shots == 0) return fail(QS_ERR_ARG, "shots must be positive");
+  if (shots == 0 || shots > kMaxShots) return fail(QS_ERR_ARG, "shots must be in [1, 2e9]");
   uint64_t fw, ow;
   const size_t need = sample_bytes(s, shots, &fw, &ow);
-  if (fw > 0xFFFFFFFFull) return fail(QS_ERR_ARG, "too many shots");
   const uint64_t M = s->n_meas;
   if (M && !record) return fail(QS_ERR_ARG, "record is NULL");
   if (record_words < M * ow) return fail(QS_ERR_SIZE, "record smaller than M * ceil(shots/64) words");
@@ -996,7 +998,7 @@ extern "C" int qs_sim_sample_noalloc(qs_sim *s, uint64_t shots, uint64_t seed, u
   if (s->resumed)
     return fail(QS_ERR_STATE, "sampling replays the op log from |0...0>; a sim restored by "
                               "qs_sim_tableau_import has none (qs_sim_reset first)");
-  if (shots == 0) return fail(QS_ERR_ARG, "shots must be positive");
+  if (shots == 0 || shots > kMaxShots) return fail(QS_ERR_ARG, "shots must be in [1, 2e9]");
   const uint32_t n = s->d.L.n;
   const uint64_t M = s->n_meas;
   const uint64_t ow = (shots + 63) / 64, fw = (ow + 3) / 4 * 4;

@@ -82,6 +82,9 @@ def test_host_checks_reject_bad_ranges_and_keep_the_sim_usable():
     bad = np.array([-2, 0], np.int64)
     assert L.qs_sim_apply_layers_dev(h, ctypes.c_void_p(dc.packed.data_ptr()),
                                      ctypes.c_void_p(bad.ctypes.data), 0, 1) == -1
+    for shots in (0, 2_000_000_001):  # refused before any allocation or launch
+        assert L.qs_sim_sample(h, shots, 1, None, 0, None, 0) == -1
+        assert L.qs_sim_sample_noalloc(h, shots, 1, None, 0) == -1
     sim.sync()
     _, orec, _ = O.run_circuit(circ, seed=5)
     assert np.array_equal(sim.record(), orec)
