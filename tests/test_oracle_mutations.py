@@ -33,6 +33,12 @@ def _pins_gates():
         TG.test_two_qubit_rules_match_conjugation(g, 1, 0)
 
 
+def _pins_golden():
+    TG.test_eq3_encoding_example()
+    TG.test_eq8_plus01_initial_tableau()
+    TG.test_example1_h1_p3()
+
+
 def _pins_measure():
     TM.test_rowsum_against_pauli_product_table()
     for n, seed in [(3, 3), (5, 4), (8, 6)]:
@@ -112,6 +118,28 @@ MUTATIONS = [
     ("noise ops share one random stream",
      "noise_p[o], qubits + op_a[o], op_b[o] - op_a[o], e++, seed,",
      "noise_p[o], qubits + op_a[o], op_b[o] - op_a[o], 0, seed,", _pins_noise),
+    ("initstate sets only the stabilizer sign",
+     "if (initstate && initstate[i]) { t->r[i] = 1; t->r[n + i] = 1; }",
+     "if (initstate && initstate[i]) { t->r[n + i] = 1; }", _pins_golden),
+    ("S dagger applied as S",
+     "case G_SDG: rule_p(t, a); rule_p(t, a); rule_p(t, a); break;",
+     "case G_SDG: rule_p(t, a); break;", _pins_gates),
+    ("CY with S and S dagger swapped",
+     "rule_p(t, b); rule_p(t, b); rule_p(t, b); rule_cx(t, a, b); rule_p(t, b); break;",
+     "rule_p(t, b); rule_cx(t, a, b); rule_p(t, b); rule_p(t, b); rule_p(t, b); break;",
+     _pins_gates),
+    ("measurement rowsum skips the destabilizers",
+     "for (int i = 0; i < 2 * n; ++i)\n      if (i != p && i != p - n && XB(t, i, q)) rowsum(t, i, p);",
+     "for (int i = n; i < 2 * n; ++i)\n      if (i != p && i != p - n && XB(t, i, q)) rowsum(t, i, p);",
+     _pins_measure),
+    ("deterministic product over every stabilizer",
+     "if (XB(t, i, q)) rowsum(t, s, i + n);", "rowsum(t, s, i + n);", _pins_measure),
+    ("frames: S acts on x instead of z",
+     "case G_S: case G_SDG: fz[a] ^= fx[a]; break;", "case G_S: case G_SDG: fx[a] ^= fz[a]; break;",
+     _pins_frames),
+    ("frames start without random Z",
+     "fz[q] = (uint8_t)((oracle_frame_word(seed, 0, (uint64_t)q, j) >> bit) & 1u);",
+     "fz[q] = 0;", _pins_frames),
 ]
 
 
@@ -135,6 +163,7 @@ def test_pins_catch_planted_mistake(name, old, new, pins):
 
 
 def test_unmutated_oracle_passes_the_same_pins():
+    _pins_golden()
     _pins_gates()
     _pins_measure()
     _pins_philox()
