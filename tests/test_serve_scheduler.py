@@ -63,3 +63,37 @@ def test_realtime_arrivals_are_respected():
     res = sch.run(_reqs([1, 1, 1], gap=0.05), realtime=True)
     for r in res:
         assert r.admit_s >= r.arrival_s - 1e-3
+
+
+def test_failing_request_releases_its_budget_and_is_reported():
+    """An exception in one request reaches the caller of run(); its memory and
+    slot are released, so every other request still completes."""
+    done = []
+
+    def execute(req, slot, admit, fp):
+        if req.rid == 1:
+            raise RuntimeError("request 1 failed")
+        time.sleep(0.01)
+        done.append(req.rid)
+        return Result(req.rid, 0, req.shots, req.arrival_s, admit, 0.0, fp)
+
+    sch = Scheduler(slots=2, budget_bytes=100, footprint=lambda r: r.shots, execute=execute)
+    with pytest.raises(RuntimeError, match="request 1 failed"):
+        sch.run(_reqs([60, 60, 60, 60]), realtime=False)
+    assert sorted(done) == [0, 2, 3]
+    assert sch.in_use == 0 and sch.active == 0
+
+
+def test_footprint_and_summary():
+    from paper_2603_14641_gb300 import qs
+    from paper_2603_14641_gb300.serve import footprint_bytes, summarize
+    base = footprint_bytes(1000, 5000, 1000, 1000)
+    assert base > qs.qs_sim_required_bytes(1000)
+    # frames (2 n words per 64 shots, rounded to 4 words) and records grow with the shots
+    more = footprint_bytes(1000, 5000, 1000, 1000 + 256)
+    assert more - base == 2 * 1000 * 4 * 8 + 3 * 1000 * 4 * 8
+    assert footprint_bytes(2000, 5000, 1000, 1000) > base
+    res = [Result(i, 10, 100, 0.0, 0.0, float(i + 1), 0) for i in range(100)]
+    s = summarize(res, makespan_s=10.0)
+    assert s["requests"] == 100 and s["shots_per_s"] == 1000.0
+    assert abs(s["p50_latency_s"] - 50.5) < 1e-9 and 99.0 < s["p99_latency_s"] <= 100.0
