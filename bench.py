@@ -194,6 +194,12 @@ WORKLOADS = {
 }
 
 
+def workload_label(name: str, n: int, depth: int, n_meas: int) -> str:
+    """config.workload of both arms (the same string for the same workload)."""
+    return (f"random Clifford circuit {name}: n={n} depth={depth} "
+            f"({n_meas} Z-measurements in the full program)")
+
+
 def step_program(circ, max_final: int):
     """The circuit's ops, with the last measurement window cut to its first
     `max_final` qubits when max_final > 0 (the full final measurement of a
@@ -341,8 +347,7 @@ def run_ours(args):
         "dtype": "u64",
         "data": "synthetic",
         "config": {
-            "workload": f"random Clifford circuit {circ.name}: n={n} depth={L} "
-                        f"({circ.n_measurements} Z-measurements in the full program)",
+            "workload": workload_label(circ.name, n, L, circ.n_measurements),
             "step": f"init + {L} gate layers + {M} measurements"
                     + (f" (the first {M} of the {n} final measurements)"
                        if args.workload == "n180k" else "")
@@ -725,7 +730,7 @@ def run_reference(args):
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": full_s * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-           "config": {"workload": f"random Clifford circuit n={args.n} depth=1000 p_cx=0.4 seed=3",
+           "config": {"workload": workload_label("n180k_d1000", args.n, args.depth, args.n),
                       "step": f"oracle gate rules on {args.cpu_rows} sampled generator rows "
                               f"through {args.cpu_layers} layers, scaled to the full 2n rows"},
            "cpu_baseline": {"value": value, "unit": "gates/s", "cores": 1, "kind": "oracle",
