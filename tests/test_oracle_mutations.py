@@ -19,6 +19,7 @@ from tests import test_oracle_frames as TF
 from tests import test_oracle_gates as TG
 from tests import test_oracle_measure as TM
 from tests import test_oracle_noise as TN
+from tests import test_oracle_subset as TSUB
 from workloads import circuits as C
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
@@ -57,6 +58,12 @@ def _pins_frames():
     TF.test_frames_support_and_distribution(5, 2, 3, 0.4)
     TF.test_frames_support_and_distribution(6, 3, 4, 0.5)
     TF.test_frames_reference_is_deterministic_part()
+
+
+def _pins_subset():
+    TSUB.test_row_subset_of_the_initial_state()
+    for n, layers, seed, nrows in [(7, 30, 1, 14), (64, 25, 2, 40)]:
+        TSUB.test_row_subset_equals_full_oracle_rows(n, layers, seed, nrows)
 
 
 def _pins_noise():
@@ -140,6 +147,11 @@ MUTATIONS = [
     ("frames start without random Z",
      "fz[q] = (uint8_t)((oracle_frame_word(seed, 0, (uint64_t)q, j) >> bit) & 1u);",
      "fz[q] = 0;", _pins_frames),
+    ("row subset seeds a stabilizer as X",
+     "else ZB(t, j, g - (uint32_t)n) = 1;", "else XB(t, j, g - (uint32_t)n) = 1;", _pins_subset),
+    ("row subset takes the stabilizer of the next qubit",
+     "else ZB(t, j, g - (uint32_t)n) = 1;",
+     "else ZB(t, j, (g - (uint32_t)n + 1u) % (uint32_t)n) = 1;", _pins_subset),
 ]
 
 
@@ -169,3 +181,4 @@ def test_unmutated_oracle_passes_the_same_pins():
     _pins_philox()
     _pins_frames()
     _pins_noise()
+    _pins_subset()
