@@ -26,6 +26,9 @@
  *     2 r_h + 2 r_i + sum_j g(x_ij, z_ij, x_hj, z_hj) mod 4, where g is the
  *     exponent of i in the single-qubit product sigma(x_ij,z_ij) *
  *     sigma(x_hj,z_hj).
+ *   - The paper's measurement variant (Sec. 3.2, Alg. 1: Stim's elimination by
+ *     CX injection) on the inverse tableau with qubit-indexed signs, with its
+ *     own gate rules for those signs (the oracle_inv_* functions below).
  *   - Pauli-frame sampling of Sec. 5 (Alg. 9) with a reference record
  *     (the frames carry flips relative to that record).
  *   - Pauli noise channels on the frames (Sec. 3 notes that frames carry
@@ -167,7 +170,10 @@ void oracle_reset(chp_t *t, const uint8_t *initstate) {
   t->last_kind = -1;
 }
 
+static void fill_g_table(void);
+
 chp_t *oracle_new(int n) {
+  fill_g_table(); /* the rowsum's g lookup (same values on every call) */
   chp_t *t = (chp_t *)calloc(1, sizeof(chp_t));
   if (!t) return NULL;
   t->n = n;
@@ -231,67 +237,73 @@ void oracle_set(chp_t *t, const uint8_t *x, const uint8_t *z, const uint8_t *r) 
   memcpy(t->x, x, cells); memcpy(t->z, z, cells); memcpy(t->r, r, (size_t)(2 * t->n));
 }
 
-/* --- Sec. 2.4, Eq. 4: the three base rules, applied to every row ------- */
+/* --- Sec. 2.4, Eq. 4: the three base rules, on one row i --------------- */
+/* Eq. 4 applies each rule to every row index i, and a row's new bits and sign
+ * depend on that row alone, so the rules are written for one row and the
+ * callers below run them over the rows. */
 
-static void rule_h(chp_t *t, int q) {
-  for (int i = 0; i < t->rows; ++i) {
-    uint8_t x = XB(t, i, q), z = ZB(t, i, q);
-    t->r[i] ^= (uint8_t)(x & z);
-    XB(t, i, q) = z;
-    ZB(t, i, q) = x;
-  }
+static void rule_h(chp_t *t, int i, int q) {
+  uint8_t x = XB(t, i, q), z = ZB(t, i, q);
+  t->r[i] ^= (uint8_t)(x & z);
+  XB(t, i, q) = z;
+  ZB(t, i, q) = x;
 }
 
-static void rule_p(chp_t *t, int q) {
-  for (int i = 0; i < t->rows; ++i) {
-    uint8_t x = XB(t, i, q), z = ZB(t, i, q);
-    t->r[i] ^= (uint8_t)(x & z);
-    ZB(t, i, q) = (uint8_t)(z ^ x);
-  }
+static void rule_p(chp_t *t, int i, int q) {
+  uint8_t x = XB(t, i, q), z = ZB(t, i, q);
+  t->r[i] ^= (uint8_t)(x & z);
+  ZB(t, i, q) = (uint8_t)(z ^ x);
 }
 
-static void rule_cx(chp_t *t, int c, int tq) {
-  for (int i = 0; i < t->rows; ++i) {
-    uint8_t xc = XB(t, i, c), zc = ZB(t, i, c), xt = XB(t, i, tq), zt = ZB(t, i, tq);
-    t->r[i] ^= (uint8_t)(xc & zt & ((xt ^ zc) ^ 1u));
-    XB(t, i, tq) = (uint8_t)(xt ^ xc);
-    ZB(t, i, c) = (uint8_t)(zc ^ zt);
-  }
+static void rule_cx(chp_t *t, int i, int c, int tq) {
+  uint8_t xc = XB(t, i, c), zc = ZB(t, i, c), xt = XB(t, i, tq), zt = ZB(t, i, tq);
+  t->r[i] ^= (uint8_t)(xc & zt & ((xt ^ zc) ^ 1u));
+  XB(t, i, tq) = (uint8_t)(xt ^ xc);
+  ZB(t, i, c) = (uint8_t)(zc ^ zt);
 }
 
 /* Pauli gates: conjugation by a Pauli flips the sign of exactly the rows
  * that anticommute with it on that qubit. */
-static void rule_pauli(chp_t *t, int q, int ax, int az) {
+static void rule_pauli(chp_t *t, int i, int q, int ax, int az) {
   /* the gate Pauli is (ax, az); a row Pauli (x, z) anticommutes with it
    * iff x*az + z*ax is odd */
-  for (int i = 0; i < t->rows; ++i)
-    t->r[i] ^= (uint8_t)((XB(t, i, q) & az) ^ (ZB(t, i, q) & ax));
+  t->r[i] ^= (uint8_t)((XB(t, i, q) & az) ^ (ZB(t, i, q) & ax));
 }
 
-void oracle_gate(chp_t *t, int type, int a, int b) {
+/* One gate on row i. */
+static void gate_row(chp_t *t, int i, int type, int a, int b) {
   switch (type) {
     case G_I: break;
-    case G_X: rule_pauli(t, a, 1, 0); break;
-    case G_Y: rule_pauli(t, a, 1, 1); break;
-    case G_Z: rule_pauli(t, a, 0, 1); break;
-    case G_H: rule_h(t, a); break;
-    case G_S: rule_p(t, a); break;
-    case G_SDG: rule_p(t, a); rule_p(t, a); rule_p(t, a); break;
-    case G_CX: rule_cx(t, a, b); break;
-    case G_CZ: rule_h(t, b); rule_cx(t, a, b); rule_h(t, b); break;
+    case G_X: rule_pauli(t, i, a, 1, 0); break;
+    case G_Y: rule_pauli(t, i, a, 1, 1); break;
+    case G_Z: rule_pauli(t, i, a, 0, 1); break;
+    case G_H: rule_h(t, i, a); break;
+    case G_S: rule_p(t, i, a); break;
+    case G_SDG: rule_p(t, i, a); rule_p(t, i, a); rule_p(t, i, a); break;
+    case G_CX: rule_cx(t, i, a, b); break;
+    case G_CZ: rule_h(t, i, b); rule_cx(t, i, a, b); rule_h(t, i, b); break;
     case G_CY: /* S_b^dag, CX, S_b in circuit order */
-      rule_p(t, b); rule_p(t, b); rule_p(t, b); rule_cx(t, a, b); rule_p(t, b); break;
-    case G_SWAP: rule_cx(t, a, b); rule_cx(t, b, a); rule_cx(t, a, b); break;
+      rule_p(t, i, b); rule_p(t, i, b); rule_p(t, i, b); rule_cx(t, i, a, b); rule_p(t, i, b); break;
+    case G_SWAP: rule_cx(t, i, a, b); rule_cx(t, i, b, a); rule_cx(t, i, a, b); break;
     case G_ISWAP: /* CZ, SWAP, S_a, S_b in circuit order */
-      oracle_gate(t, G_CZ, a, b); oracle_gate(t, G_SWAP, a, b); rule_p(t, a); rule_p(t, b); break;
+      gate_row(t, i, G_CZ, a, b); gate_row(t, i, G_SWAP, a, b); rule_p(t, i, a); rule_p(t, i, b); break;
     default: break;
   }
 }
 
-/* gates: count rows of (type, q0, q1) */
+void oracle_gate(chp_t *t, int type, int a, int b) {
+  for (int i = 0; i < t->rows; ++i) gate_row(t, i, type, a, b);
+}
+
+/* gates: count rows of (type, q0, q1), applied in order. Every row goes
+ * through the whole list before the next row starts: rows evolve
+ * independently (Eq. 4 acts on each row index on its own), so this gives the
+ * same tableau as applying gate by gate to all rows, while each row's bytes
+ * stay in cache. */
 void oracle_apply(chp_t *t, const uint32_t *gates, long count) {
-  for (long g = 0; g < count; ++g)
-    oracle_gate(t, (int)gates[3 * g], (int)gates[3 * g + 1], (int)gates[3 * g + 2]);
+  for (int i = 0; i < t->rows; ++i)
+    for (long g = 0; g < count; ++g)
+      gate_row(t, i, (int)gates[3 * g], (int)gates[3 * g + 1], (int)gates[3 * g + 2]);
 }
 
 /* --- rowsum (Aaronson & Gottesman), cited in Sec. 2.5 ------------------ */
@@ -304,12 +316,20 @@ static int g_fn(int x1, int z1, int x2, int z2) {
   return x2 * (1 - 2 * z2);                         /* Z * . */
 }
 
+/* g_fn tabulated over its 16 arguments, index 8 x1 + 4 z1 + 2 x2 + z2 (a
+ * lookup instead of branches on random bits; filled from g_fn itself) */
+static int g_table[16];
+
+static void fill_g_table(void) {
+  for (int v = 0; v < 16; ++v) g_table[v] = g_fn((v >> 3) & 1, (v >> 2) & 1, (v >> 1) & 1, v & 1);
+}
+
 /* row h <- row i * row h (generator product), sign from the mod-4 phase */
 static void rowsum(chp_t *t, int h, int i) {
   int n = t->n;
   long sum = 2 * (long)t->r[h] + 2 * (long)t->r[i];
   for (int j = 0; j < n; ++j)
-    sum += g_fn(XB(t, i, j), ZB(t, i, j), XB(t, h, j), ZB(t, h, j));
+    sum += g_table[8 * XB(t, i, j) + 4 * ZB(t, i, j) + 2 * XB(t, h, j) + ZB(t, h, j)];
   long m = ((sum % 4) + 4) % 4;
   if (m == 1 || m == 3) t->odd_phase_count++;
   t->r[h] = (uint8_t)(m == 2);
@@ -470,4 +490,242 @@ int oracle_frames(int n, const uint32_t *gates, const uint32_t *qubits, const in
   }
   free(fx); free(fz);
   return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Inverse tableau with qubit-indexed signs: the representation of the  */
+/* paper's measurement variant (Sec. 3.2, Alg. 1; Stim's TableauSimulator) */
+/* ------------------------------------------------------------------ */
+/*
+ * For the Clifford C that prepares the state from |0...0>, this mode keeps
+ * the Pauli strings C^dag Z_q C and C^dag X_q C over the input qubits, one per
+ * qubit q, each with a sign. Their bits are the bits of the extended tableau
+ * of Sec. 2.5 read by columns. With XS[i][q] the x bit of stabilizer i at
+ * qubit q (row n + i of x), XD[i][q] the x bit of destabilizer i (row i of
+ * x), and ZS, ZD the same for z,
+ *   C^dag Z_q C = (-1)^ss[q] * prod_i sigma(XS[i][q], XD[i][q])   (x, z at input i)
+ *   C^dag X_q C = (-1)^sd[q] * prod_i sigma(ZS[i][q], ZD[i][q]).
+ * (C^dag P C anticommutes with Z_i iff P anticommutes with C Z_i C^dag =
+ * stabilizer i, and with X_i iff P anticommutes with destabilizer i.) The
+ * sign vectors S_S and S_D of Alg. 1 are ss and sd, indexed by qubit (the
+ * paper's reading G2: these signs belong to the inverse tableau, not to the
+ * forward generators).
+ *
+ * A gate G appended to the circuit turns C into G C, so every image becomes
+ * that of G^dag P G: the bits follow the column rules of Eq. 4 (same bits as
+ * the forward tableau), and the signs of the gate's qubits follow from the
+ * phase of a product of two images. A measurement runs Alg. 1: pivot = the
+ * smallest stabilizer index with XS[p][q] = 1; CX injections from the pivot
+ * into every later anticommuting stabilizer (in index order); the pivot is
+ * swapped for a commuting generator by an H or an H_YZ injection; an X
+ * injection sets the outcome to the coin. A deterministic outcome is ss[q].
+ */
+typedef struct {
+  int n;
+  uint8_t *x, *z;   /* 2n rows of n bits, as in chp_t */
+  uint8_t *ss, *sd; /* n sign bits each */
+  int last_kind;    /* 1 = last measurement was probabilistic, 0 = deterministic */
+  long odd_count;   /* products of images whose phase had the wrong parity (must stay 0) */
+} inv_t;
+
+#define IXB(t, i, j) ((t)->x[(size_t)(i) * (size_t)(t)->n + (size_t)(j)])
+#define IZB(t, i, j) ((t)->z[(size_t)(i) * (size_t)(t)->n + (size_t)(j)])
+
+void oracle_inv_reset(inv_t *t, const uint8_t *initstate) {
+  int n = t->n;
+  memset(t->x, 0, (size_t)(2 * n) * n);
+  memset(t->z, 0, (size_t)(2 * n) * n);
+  for (int i = 0; i < n; ++i) {
+    IXB(t, i, i) = 1;     /* destabilizer i = X_i: C^dag Z_i C has z at input i */
+    IZB(t, n + i, i) = 1; /* stabilizer i = Z_i: C^dag X_i C has x at input i */
+    /* |1> on qubit i is X_i|0>: X_i Z_i X_i = -Z_i, X_i X_i X_i = X_i */
+    t->ss[i] = (uint8_t)(initstate && initstate[i] ? 1 : 0);
+    t->sd[i] = 0;
+  }
+  t->last_kind = -1;
+  t->odd_count = 0;
+}
+
+inv_t *oracle_inv_new(int n) {
+  fill_g_table();
+  inv_t *t = (inv_t *)calloc(1, sizeof(inv_t));
+  if (!t) return NULL;
+  t->n = n;
+  size_t cells = (size_t)(2 * n) * (size_t)(n > 0 ? n : 1);
+  t->x = (uint8_t *)calloc(cells, 1);
+  t->z = (uint8_t *)calloc(cells, 1);
+  t->ss = (uint8_t *)calloc((size_t)n + 1, 1);
+  t->sd = (uint8_t *)calloc((size_t)n + 1, 1);
+  if (!t->x || !t->z || !t->ss || !t->sd) {
+    free(t->x); free(t->z); free(t->ss); free(t->sd); free(t);
+    return NULL;
+  }
+  oracle_inv_reset(t, NULL);
+  return t;
+}
+
+void oracle_inv_free(inv_t *t) {
+  if (!t) return;
+  free(t->x); free(t->z); free(t->ss); free(t->sd); free(t);
+}
+
+/* x, z: 2n*n bytes (rows as in oracle_get); ss, sd: n bytes */
+void oracle_inv_get(const inv_t *t, uint8_t *x, uint8_t *z, uint8_t *ss, uint8_t *sd) {
+  size_t cells = (size_t)(2 * t->n) * t->n;
+  memcpy(x, t->x, cells); memcpy(z, t->z, cells);
+  memcpy(ss, t->ss, (size_t)t->n); memcpy(sd, t->sd, (size_t)t->n);
+}
+
+int oracle_inv_last_kind(const inv_t *t) { return t->last_kind; }
+long oracle_inv_odd_count(const inv_t *t) { return t->odd_count; }
+
+/* bits at input i of the image of X_q (w = 0) or Z_q (w = 1) */
+static int img_x(const inv_t *t, int w, int q, int i) { return w ? IXB(t, t->n + i, q) : IZB(t, t->n + i, q); }
+static int img_z(const inv_t *t, int w, int q, int i) { return w ? IXB(t, i, q) : IZB(t, i, q); }
+
+/* image(P_a) * image(P_b) = i^e * sigma(bitwise sum); returns e mod 4 */
+static int img_product_phase(const inv_t *t, int wa, int a, int wb, int b) {
+  long e = 0;
+  for (int i = 0; i < t->n; ++i)
+    e += g_fn(img_x(t, wa, a, i), img_z(t, wa, a, i), img_x(t, wb, b, i), img_z(t, wb, b, i));
+  return (int)(((e % 4) + 4) % 4);
+}
+
+/* H: H X H = Z and H Z H = X, so the two images of qubit a trade places
+ * (bits: x_a <-> z_a in every row, Eq. 4) */
+static void inv_h(inv_t *t, int a) {
+  uint8_t s = t->ss[a];
+  t->ss[a] = t->sd[a];
+  t->sd[a] = s;
+  for (int i = 0; i < 2 * t->n; ++i) {
+    uint8_t x = IXB(t, i, a);
+    IXB(t, i, a) = IZB(t, i, a);
+    IZB(t, i, a) = x;
+  }
+}
+
+/* S (dagger = 0) or S^dag (dagger = 1): S^dag X S = -Y and S X S^dag = Y with
+ * Y = i X Z; Z is fixed. The new image of X_a is -i (resp. i) times
+ * image(X_a) image(Z_a) (bits: z_a ^= x_a in every row). */
+static void inv_s(inv_t *t, int a, int dagger) {
+  int e = img_product_phase(t, 0, a, 1, a);
+  int f = (e + (dagger ? 1 : 3)) & 3; /* times i (= i^1) or -i (= i^3) */
+  if (f & 1) t->odd_count++;         /* the images of X_a and Z_a anticommute: e is odd */
+  t->sd[a] = (uint8_t)(t->sd[a] ^ t->ss[a] ^ (f >> 1));
+  for (int i = 0; i < 2 * t->n; ++i) IZB(t, i, a) ^= IXB(t, i, a);
+}
+
+/* CX (control c, target tq): X_c -> X_c X_t and Z_t -> Z_c Z_t under
+ * conjugation; X_t and Z_c are fixed (bits: x_t ^= x_c, z_c ^= z_t). */
+static void inv_cx(inv_t *t, int c, int tq) {
+  int e1 = img_product_phase(t, 0, c, 0, tq); /* image(X_c) image(X_t), commuting: even */
+  int e2 = img_product_phase(t, 1, c, 1, tq); /* image(Z_c) image(Z_t), commuting: even */
+  if ((e1 | e2) & 1) t->odd_count++;
+  t->sd[c] = (uint8_t)(t->sd[c] ^ t->sd[tq] ^ (e1 >> 1));
+  t->ss[tq] = (uint8_t)(t->ss[tq] ^ t->ss[c] ^ (e2 >> 1));
+  for (int i = 0; i < 2 * t->n; ++i) {
+    IXB(t, i, tq) ^= IXB(t, i, c);
+    IZB(t, i, c) ^= IZB(t, i, tq);
+  }
+}
+
+void oracle_inv_gate(inv_t *t, int type, int a, int b) {
+  switch (type) {
+    case G_I: break;
+    case G_X: t->ss[a] ^= 1u; break;                /* X Z X = -Z */
+    case G_Z: t->sd[a] ^= 1u; break;                /* Z X Z = -X */
+    case G_Y: t->ss[a] ^= 1u; t->sd[a] ^= 1u; break; /* Y anticommutes with X and Z */
+    case G_H: inv_h(t, a); break;
+    case G_S: inv_s(t, a, 0); break;
+    case G_SDG: inv_s(t, a, 1); break;
+    case G_CX: inv_cx(t, a, b); break;
+    case G_CZ: inv_h(t, b); inv_cx(t, a, b); inv_h(t, b); break;
+    case G_CY: inv_s(t, b, 1); inv_cx(t, a, b); inv_s(t, b, 0); break;
+    case G_SWAP: inv_cx(t, a, b); inv_cx(t, b, a); inv_cx(t, a, b); break;
+    case G_ISWAP:
+      oracle_inv_gate(t, G_CZ, a, b); oracle_inv_gate(t, G_SWAP, a, b);
+      inv_s(t, a, 0); inv_s(t, b, 0); break;
+    default: break;
+  }
+}
+
+void oracle_inv_apply(inv_t *t, const uint32_t *gates, long count) {
+  for (long g = 0; g < count; ++g)
+    oracle_inv_gate(t, (int)gates[3 * g], (int)gates[3 * g + 1], (int)gates[3 * g + 2]);
+}
+
+/* Alg. 1's injections, element by element over the n qubit positions of the
+ * rows they are given (s: a sign vector indexed by qubit). */
+static void inject_cx(int n, uint8_t *s, const uint8_t *xc, uint8_t *zc, uint8_t *xt, const uint8_t *zt) {
+  for (int j = 0; j < n; ++j) {
+    s[j] ^= (uint8_t)(xc[j] & zt[j] & ((zc[j] ^ xt[j]) ^ 1u));
+    xt[j] ^= xc[j];
+    zc[j] ^= zt[j];
+  }
+}
+
+static void inject_invp(int n, uint8_t *s, uint8_t *x, const uint8_t *z) {
+  for (int j = 0; j < n; ++j) {
+    s[j] ^= (uint8_t)(x[j] & (z[j] ^ 1u));
+    x[j] ^= z[j];
+  }
+}
+
+static void inject_had(int n, uint8_t *s, uint8_t *x, uint8_t *z) {
+  for (int j = 0; j < n; ++j) {
+    s[j] ^= (uint8_t)(x[j] & z[j]);
+    uint8_t v = x[j];
+    x[j] = z[j];
+    z[j] = v;
+  }
+}
+
+static void inject_x(int n, uint8_t *s, const uint8_t *z) {
+  for (int j = 0; j < n; ++j) s[j] ^= z[j];
+}
+
+/* Z-measurement of qubit q (Alg. 1, ProbabilisticMeasurement); the coin is
+ * coin(seed, shot, midx). Rows: XS[i] = x row n + i, XD[i] = x row i, ZS[i]
+ * = z row n + i, ZD[i] = z row i. */
+int oracle_inv_measure(inv_t *t, int q, uint64_t seed, uint64_t shot, uint64_t midx) {
+  int n = t->n;
+  int p = -1;
+  for (int i = 0; i < n; ++i)
+    if (IXB(t, n + i, q)) { p = i; break; }
+  if (p < 0) {
+    t->last_kind = 0;
+    return t->ss[q];
+  }
+  t->last_kind = 1;
+  uint8_t *XSp = &IXB(t, n + p, 0), *XDp = &IXB(t, p, 0), *ZSp = &IZB(t, n + p, 0), *ZDp = &IZB(t, p, 0);
+  /* GE: CX injections from the pivot into the later anticommuting stabilizers, in order */
+  for (int tg = p + 1; tg < n; ++tg) {
+    if (!IXB(t, n + tg, q)) continue;
+    inject_cx(n, t->sd, ZSp, ZDp, &IZB(t, n + tg, 0), &IZB(t, tg, 0));
+    inject_cx(n, t->ss, XSp, XDp, &IXB(t, n + tg, 0), &IXB(t, tg, 0));
+  }
+  /* swap the anticommuting stabilizer for a commuting one: the Y case takes
+   * H_YZ (InvP), the X case H */
+  if (XDp[q]) {
+    inject_invp(n, t->sd, ZSp, ZDp);
+    inject_invp(n, t->ss, XSp, XDp);
+  } else {
+    inject_had(n, t->sd, ZSp, ZDp);
+    inject_had(n, t->ss, XSp, XDp);
+  }
+  /* the outcome is the coin: an X injection on the pivot flips it if needed */
+  int m = oracle_coin(seed, shot, midx);
+  if (t->ss[q] != (uint8_t)m) {
+    inject_x(n, t->sd, ZDp);
+    inject_x(n, t->ss, XDp);
+  }
+  return t->ss[q];
+}
+
+void oracle_inv_measure_many(inv_t *t, const uint32_t *qubits, long count, uint64_t seed,
+                             uint64_t shot, uint64_t midx0, uint8_t *out, uint8_t *kind) {
+  for (long i = 0; i < count; ++i) {
+    out[i] = (uint8_t)oracle_inv_measure(t, (int)qubits[i], seed, shot, midx0 + (uint64_t)i);
+    if (kind) kind[i] = (uint8_t)t->last_kind;
+  }
 }

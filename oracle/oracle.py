@@ -81,6 +81,22 @@ def load_library(path: str):
     L.oracle_noise_draw.argtypes = [ctypes.c_uint64] * 4 + [_u64p, _u64p]
     L.oracle_noise_threshold.restype = ctypes.c_uint64
     L.oracle_noise_threshold.argtypes = [ctypes.c_double]
+    L.oracle_inv_new.restype = ctypes.c_void_p
+    L.oracle_inv_new.argtypes = [ctypes.c_int]
+    L.oracle_inv_free.argtypes = [ctypes.c_void_p]
+    L.oracle_inv_reset.argtypes = [ctypes.c_void_p, _u8p]
+    L.oracle_inv_get.argtypes = [ctypes.c_void_p, _u8p, _u8p, _u8p, _u8p]
+    L.oracle_inv_gate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.oracle_inv_apply.argtypes = [ctypes.c_void_p, _u32p, ctypes.c_long]
+    L.oracle_inv_measure.restype = ctypes.c_int
+    L.oracle_inv_measure.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                     ctypes.c_uint64, ctypes.c_uint64]
+    L.oracle_inv_measure_many.argtypes = [ctypes.c_void_p, _u32p, ctypes.c_long, ctypes.c_uint64,
+                                          ctypes.c_uint64, ctypes.c_uint64, _u8p, _u8p]
+    L.oracle_inv_last_kind.restype = ctypes.c_int
+    L.oracle_inv_last_kind.argtypes = [ctypes.c_void_p]
+    L.oracle_inv_odd_count.restype = ctypes.c_long
+    L.oracle_inv_odd_count.argtypes = [ctypes.c_void_p]
     return L
 
 
@@ -293,3 +309,84 @@ def frames(circuit, ref: np.ndarray, shots: int, seed: int) -> np.ndarray:
     if rc != 0:
         raise MemoryError("oracle_frames failed")
     return out[:M]
+
+
+class InverseOracle:
+    """The inverse tableau with qubit-indexed signs (Sec. 3.2, Alg. 1): for
+    the Clifford C preparing the state, the images C^dag Z_q C (sign ss[q], x
+    bits XS[:, q], z bits XD[:, q]) and C^dag X_q C (sign sd[q], bits ZS[:, q],
+    ZD[:, q]); its bits are the extended tableau's (rows 0..n-1 destabilizers,
+    n..2n-1 stabilizers). Measurement follows Alg. 1 with the keyed coin."""
+
+    def __init__(self, n: int, initstate: Optional[np.ndarray] = None):
+        self.n = int(n)
+        self._h = lib().oracle_inv_new(self.n)
+        if not self._h:
+            raise MemoryError("oracle_inv_new failed")
+        self.midx = 0
+        if initstate is not None:
+            self.reset(initstate)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().oracle_inv_free(h)
+            self._h = None
+
+    def reset(self, initstate: Optional[np.ndarray] = None) -> None:
+        if initstate is None:
+            lib().oracle_inv_reset(self._h, None)
+        else:
+            s = np.ascontiguousarray(initstate, np.uint8)
+            lib().oracle_inv_reset(self._h, _p(s, _u8p))
+        self.midx = 0
+
+    def gate(self, t: int, a: int, b: int = 0) -> None:
+        lib().oracle_inv_gate(self._h, int(t), int(a), int(b))
+
+    def apply(self, gates: np.ndarray) -> None:
+        g = np.ascontiguousarray(gates, np.uint32)
+        if g.size:
+            lib().oracle_inv_apply(self._h, _p(g, _u32p), g.shape[0])
+
+    def measure(self, qubits, seed: int, shot: int = 0):
+        q = np.ascontiguousarray(qubits, np.uint32)
+        out = np.zeros(len(q), np.uint8)
+        kind = np.zeros(len(q), np.uint8)
+        if len(q):
+            lib().oracle_inv_measure_many(self._h, _p(q, _u32p), len(q), seed, shot, self.midx,
+                                          _p(out, _u8p), _p(kind, _u8p))
+        self.midx += len(q)
+        return out, kind
+
+    def get(self):
+        """(x, z, ss, sd): x, z of shape (2n, n), ss and sd of shape (n,)."""
+        n = self.n
+        x = np.zeros((2 * n, n), np.uint8)
+        z = np.zeros((2 * n, n), np.uint8)
+        ss = np.zeros(n, np.uint8)
+        sd = np.zeros(n, np.uint8)
+        lib().oracle_inv_get(self._h, _p(x, _u8p), _p(z, _u8p), _p(ss, _u8p), _p(sd, _u8p))
+        return x, z, ss, sd
+
+    @property
+    def odd_count(self) -> int:
+        return int(lib().oracle_inv_odd_count(self._h))
+
+
+def run_circuit_inverse(circuit, seed: int, shot: int = 0,
+                        oracle: Optional[InverseOracle] = None):
+    """As run_circuit, on the inverse tableau (Alg. 1's measurement).
+    Returns (oracle, record, kinds)."""
+    o = oracle or InverseOracle(circuit.n)
+    rec, kinds = [], []
+    for op in circuit.ops:
+        if op[0] == "layers":
+            o.apply(circuit.gates[circuit.layer_ptr[op[1]]:circuit.layer_ptr[op[2]]])
+        elif op[0] == "measure":
+            out, kind = o.measure(op[1], seed, shot)
+            rec.append(out)
+            kinds.append(kind)
+    rec = np.concatenate(rec) if rec else np.zeros(0, np.uint8)
+    kinds = np.concatenate(kinds) if kinds else np.zeros(0, np.uint8)
+    return o, rec, kinds

@@ -17,6 +17,7 @@ import pytest
 from oracle import oracle as O
 from tests import test_oracle_frames as TF
 from tests import test_oracle_gates as TG
+from tests import test_oracle_inverse as TI
 from tests import test_oracle_measure as TM
 from tests import test_oracle_noise as TN
 from tests import test_oracle_subset as TSUB
@@ -66,6 +67,19 @@ def _pins_subset():
         TSUB.test_row_subset_equals_full_oracle_rows(n, layers, seed, nrows)
 
 
+def _pins_inverse():
+    for n, seed in [(1, 1), (2, 2), (3, 4)]:
+        TI.test_images_match_unitary_conjugation(n, seed)
+    for g in (C.X, C.Y, C.Z, C.H, C.S, C.SDG, C.CX, C.CY, C.CZ, C.SWAP, C.ISWAP):
+        TI.test_each_gate_alone_matches_unitary(g)
+    for n, seed in [(3, 2), (6, 3), (12, 4), (40, 5)]:
+        TI.test_records_and_state_equal_chp(n, seed)
+    for n, seed in [(2, 4), (3, 5), (4, 6)]:
+        TI.test_measurement_is_right_multiplication_by_injected_gates(n, seed)
+    TI.test_state_vector_measurement_distribution()
+    TI.test_initstate_is_measured_deterministically()
+
+
 def _pins_noise():
     for seed in (1, 2, 3):
         TN.test_noisy_frames_match_exact_distribution(seed)
@@ -80,12 +94,12 @@ MUTATIONS = [
      "t->r[i] ^= (uint8_t)(xc & zt & ((xt ^ zc) ^ 1u));",
      "t->r[i] ^= (uint8_t)(xc & zt & (xt ^ zc));", _pins_gates),
     ("H forgets the sign",
-     "    t->r[i] ^= (uint8_t)(x & z);\n    XB(t, i, q) = z;",
-     "    XB(t, i, q) = z;", _pins_gates),
+     "  t->r[i] ^= (uint8_t)(x & z);\n  XB(t, i, q) = z;",
+     "  XB(t, i, q) = z;", _pins_gates),
     ("CX updates the wrong z column",
      "ZB(t, i, c) = (uint8_t)(zc ^ zt);", "ZB(t, i, tq) = (uint8_t)(zt ^ zc);", _pins_gates),
     ("Pauli Z flips on z instead of x",
-     "case G_Z: rule_pauli(t, a, 0, 1); break;", "case G_Z: rule_pauli(t, a, 1, 0); break;",
+     "case G_Z: rule_pauli(t, i, a, 0, 1); break;", "case G_Z: rule_pauli(t, i, a, 1, 0); break;",
      _pins_gates),
     ("g function: wrong sign for X * .",
      "return z2 * (2 * x2 - 1); /* X * . */", "return z2 * (1 - 2 * x2); /* X * . */",
@@ -94,8 +108,8 @@ MUTATIONS = [
      "long sum = 2 * (long)t->r[h] + 2 * (long)t->r[i];", "long sum = 2 * (long)t->r[h];",
      _pins_measure),
     ("rowsum transposes x and z of the target",
-     "sum += g_fn(XB(t, i, j), ZB(t, i, j), XB(t, h, j), ZB(t, h, j));",
-     "sum += g_fn(XB(t, i, j), ZB(t, i, j), ZB(t, h, j), XB(t, h, j));", _pins_measure),
+     "sum += g_table[8 * XB(t, i, j) + 4 * ZB(t, i, j) + 2 * XB(t, h, j) + ZB(t, h, j)];",
+     "sum += g_table[8 * XB(t, i, j) + 4 * ZB(t, i, j) + 2 * ZB(t, h, j) + XB(t, h, j)];", _pins_measure),
     ("deterministic product uses destabilizers",
      "if (XB(t, i, q)) rowsum(t, s, i + n);", "if (XB(t, i, q)) rowsum(t, s, i);", _pins_measure),
     ("pivot searched among destabilizers",
@@ -129,11 +143,11 @@ MUTATIONS = [
      "if (initstate && initstate[i]) { t->r[i] = 1; t->r[n + i] = 1; }",
      "if (initstate && initstate[i]) { t->r[n + i] = 1; }", _pins_golden),
     ("S dagger applied as S",
-     "case G_SDG: rule_p(t, a); rule_p(t, a); rule_p(t, a); break;",
-     "case G_SDG: rule_p(t, a); break;", _pins_gates),
+     "case G_SDG: rule_p(t, i, a); rule_p(t, i, a); rule_p(t, i, a); break;",
+     "case G_SDG: rule_p(t, i, a); break;", _pins_gates),
     ("CY with S and S dagger swapped",
-     "rule_p(t, b); rule_p(t, b); rule_p(t, b); rule_cx(t, a, b); rule_p(t, b); break;",
-     "rule_p(t, b); rule_cx(t, a, b); rule_p(t, b); rule_p(t, b); rule_p(t, b); break;",
+     "rule_p(t, i, b); rule_p(t, i, b); rule_p(t, i, b); rule_cx(t, i, a, b); rule_p(t, i, b); break;",
+     "rule_p(t, i, b); rule_cx(t, i, a, b); rule_p(t, i, b); rule_p(t, i, b); rule_p(t, i, b); break;",
      _pins_gates),
     ("measurement rowsum skips the destabilizers",
      "for (int i = 0; i < 2 * n; ++i)\n      if (i != p && i != p - n && XB(t, i, q)) rowsum(t, i, p);",
@@ -147,6 +161,31 @@ MUTATIONS = [
     ("frames start without random Z",
      "fz[q] = (uint8_t)((oracle_frame_word(seed, 0, (uint64_t)q, j) >> bit) & 1u);",
      "fz[q] = 0;", _pins_frames),
+    ("inverse: CX injection sign drops the negation",
+     "s[j] ^= (uint8_t)(xc[j] & zt[j] & ((zc[j] ^ xt[j]) ^ 1u));",
+     "s[j] ^= (uint8_t)(xc[j] & zt[j] & (zc[j] ^ xt[j]));", _pins_inverse),
+    ("inverse: CX injection leaves the pivot's z row alone",
+     "    xt[j] ^= xc[j];\n    zc[j] ^= zt[j];", "    xt[j] ^= xc[j];", _pins_inverse),
+    ("inverse: swap case decided on the stabilizer bit",
+     "  if (XDp[q]) {", "  if (XSp[q]) {", _pins_inverse),
+    ("inverse: X injection flips ss by the z row",
+     "inject_x(n, t->ss, XDp);", "inject_x(n, t->ss, ZDp);", _pins_inverse),
+    ("inverse: S and S dagger signs swapped",
+     "int f = (e + (dagger ? 1 : 3)) & 3;", "int f = (e + (dagger ? 3 : 1)) & 3;", _pins_inverse),
+    ("inverse: CX forgets the control's Z sign",
+     "t->ss[tq] = (uint8_t)(t->ss[tq] ^ t->ss[c] ^ (e2 >> 1));",
+     "t->ss[tq] = (uint8_t)(t->ss[tq] ^ (e2 >> 1));", _pins_inverse),
+    ("inverse: H keeps the signs in place",
+     "  uint8_t s = t->ss[a];\n  t->ss[a] = t->sd[a];\n  t->sd[a] = s;\n", "", _pins_inverse),
+    ("inverse: initstate signs the X image",
+     "    t->ss[i] = (uint8_t)(initstate && initstate[i] ? 1 : 0);\n    t->sd[i] = 0;",
+     "    t->sd[i] = (uint8_t)(initstate && initstate[i] ? 1 : 0);\n    t->ss[i] = 0;", _pins_inverse),
+    ("inverse: deterministic outcome read from sd",
+     "    t->last_kind = 0;\n    return t->ss[q];", "    t->last_kind = 0;\n    return t->sd[q];",
+     _pins_inverse),
+    ("inverse: H_YZ injection forgets the bit update",
+     "    x[j] ^= z[j];\n  }\n}\n\nstatic void inject_had", "  }\n}\n\nstatic void inject_had",
+     _pins_inverse),
     ("row subset seeds a stabilizer as X",
      "else ZB(t, j, g - (uint32_t)n) = 1;", "else XB(t, j, g - (uint32_t)n) = 1;", _pins_subset),
     ("row subset takes the stabilizer of the next qubit",
@@ -182,3 +221,4 @@ def test_unmutated_oracle_passes_the_same_pins():
     _pins_frames()
     _pins_noise()
     _pins_subset()
+    _pins_inverse()
