@@ -94,6 +94,13 @@ typedef struct qs_options {
  * words or more (about 371,000 qubits and up); the flag runs that code path on
  * a tableau of any size (identical results). */
 #define QS_FLAG_WIDE_OFFSETS 8u
+/* qs_options.flags: run the blocked measurement's symbolic pass (which rows
+ * each of a block's measurements targets) as one launch per measurement over
+ * every row. By default that launch sequence is used only above 25,600 qubits;
+ * up to that size one CTA runs every step over the stabilizer rows held in
+ * shared memory. The flag runs the large-size code path at any size
+ * (identical results). */
+#define QS_FLAG_STEP_SYMBOLIC 16u
 
 typedef struct qs_sim qs_sim;
 
@@ -458,6 +465,42 @@ const char *qs_schedule_last_error(void);
 
 /* Number of kernel launches the sim has enqueued so far. */
 uint64_t qs_sim_launch_count(const qs_sim *sim);
+
+/* Kernel classes of qs_sim_timing (the phases of Alg. 2 and of the blocked
+ * measurement): gate layers (Sec. 4.4), the layout switch between column- and
+ * row-major (Sec. 4.5), the blocked measurement's symbolic pass, its pivot
+ * rows and their signs, its apply pass over the row-major tableau and its
+ * per-row signs and record, measurements outside blocks (single and
+ * pipelined), and frame sampling (Sec. 5). */
+enum {
+  QS_TIME_GATES = 0,
+  QS_TIME_TRANSPOSE = 1,
+  QS_TIME_BLK_SYMBOLIC = 2,
+  QS_TIME_BLK_PIVOT_ROWS = 3,
+  QS_TIME_BLK_APPLY = 4,
+  QS_TIME_BLK_SIGNS = 5,
+  QS_TIME_MEASURE_SINGLE = 6,
+  QS_TIME_SAMPLE = 7,
+  QS_NUM_TIME_KINDS = 8
+};
+
+/*
+ * Turns CUDA-event timing of the kernel classes on (on != 0) or off and
+ * clears the totals. While on, the sim records an event pair on its stream
+ * around each group of launches of one class (one pair per call, layout
+ * switch or block phase); the events only timestamp the stream, the kernels
+ * are unchanged. Off by default. The paper has no counterpart; it times its
+ * phases the same way (Sec. 6 tables).
+ */
+int qs_sim_set_timing(qs_sim *sim, int on);
+
+/*
+ * Waits for the stream and writes, for kind k < kinds (at most
+ * QS_NUM_TIME_KINDS), the summed device milliseconds ms[k] and the number of
+ * timed groups count[k] since timing was turned on. Either pointer may be
+ * NULL. Errors: QS_ERR_ARG (NULL sim), QS_ERR_STATE (timing is off).
+ */
+int qs_sim_timing(qs_sim *sim, double *ms, uint64_t *count, uint32_t kinds);
 
 #ifdef __cplusplus
 }

@@ -655,11 +655,12 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
     return e;
   });
   if (ea != cudaSuccess) return ea;
+  tbegin(d.timer, QS_TIME_BLK_SYMBOLIC, s);
   blk_reset_kernel<<<1, 64, 0, s>>>(st, B);
   blk_init_kernel<<<rb, 256, 0, s>>>(d.RX, L.rs, L.nrows, L.n, L.k, qubits, B, C0, M, base, st,
                                      d.err);
   int sym_launches = B;
-  if (L.n <= kSymSmallRows) {
+  if (L.n <= kSymSmallRows && !d.step_symbolic) {
     blk_symbolic_small_kernel<<<1, kSymThreads, (size_t)L.n * sizeof(uint64_t), s>>>(L.n, L.k, B, C0,
                                                                                      st);
     blk_replay_kernel<<<rb, 256, 0, s>>>(L.nrows, L.k, C0, M, base, st);
@@ -669,22 +670,29 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
       blk_step_kernel<<<rb, 256, 0, s>>>(L.nrows, L.n, L.k, j, B, (j & 1) ? C1 : C0,
                                          (j & 1) ? C0 : C1, M, base, st);
   }
+  tend(d.timer, QS_TIME_BLK_SYMBOLIC, s);
+  tbegin(d.timer, QS_TIME_BLK_PIVOT_ROWS, s);
   blk_vrows_kernel<<<dim3(chunks, kVrowSplit), kVrowThreads, kVrowSmem, s>>>(d.RX, d.RZ, L.rs, VX,
                                                                               VZ, st);
   blk_signs_kernel<<<1, 64, 0, s>>>(d.S, st, d.err);
+  tend(d.timer, QS_TIME_BLK_PIVOT_ROWS, s);
   // about 8 waves of one block per SM (the table takes 200 KB of shared memory),
   // but at least 512 rows per block so that building the 200 KB table stays
   // small next to the rows it serves
   const uint32_t rows_y = std::max<uint32_t>(
       1, (uint32_t)std::min<uint64_t>(((uint64_t)d.sms * 8 + chunks - 1) / chunks, L.nrows / 512));
+  tbegin(d.timer, QS_TIME_BLK_APPLY, s);
   if (!d.wide_offsets && (uint64_t)L.nrows * L.rs < (1ull << 32))
     blk_apply_kernel<uint32_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
         d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, M, base, Tp, st);
   else
     blk_apply_kernel<uint64_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
         d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, M, base, Tp, st);
+  tend(d.timer, QS_TIME_BLK_APPLY, s);
+  tbegin(d.timer, QS_TIME_BLK_SIGNS, s);
   blk_rows_kernel<<<rb, 256, 0, s>>>(d.S, L.nrows, qubits, M, base, Tp, chunks, st, m0, key.seed,
                                      key.shot, d.record, d.kinds, d.err);
+  tend(d.timer, QS_TIME_BLK_SIGNS, s);
   if (launches) *launches += 6 + sym_launches;
   if (len_dev) *len_dev = &st->len;
   return cudaGetLastError();

@@ -102,6 +102,70 @@ inline cudaError_t once_per_device(std::atomic<uint64_t> &done, F set) {
   return e;
 }
 
+// Optional CUDA-event timing of kernel classes (qs_sim_set_timing): begin/end
+// record an event pair on the stream around a group of launches; pairs are
+// resolved into elapsed milliseconds once their end event has completed.
+// Kinds are the QS_TIME_* values of qs.h.
+struct KernelTimer {
+  double ms[QS_NUM_TIME_KINDS] = {};
+  uint64_t count[QS_NUM_TIME_KINDS] = {};
+  struct Pair { int kind; cudaEvent_t a, b; };
+  std::vector<Pair> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t open[QS_NUM_TIME_KINDS] = {};
+
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+  }
+  void begin(int kind, cudaStream_t s) {
+    if (open[kind]) { pool.push_back(open[kind]); open[kind] = nullptr; }  // left open by an error
+    cudaEvent_t e = get();
+    if (e && cudaEventRecord(e, s) == cudaSuccess) open[kind] = e;
+  }
+  void end(int kind, cudaStream_t s) {
+    cudaEvent_t a = open[kind];
+    open[kind] = nullptr;
+    if (!a) return;
+    cudaEvent_t b = get();
+    if (!b || cudaEventRecord(b, s) != cudaSuccess) { pool.push_back(a); return; }
+    pending.push_back({kind, a, b});
+  }
+  // adds the pairs whose end event has completed (all of them after a sync)
+  void resolve() {
+    size_t keep = 0;
+    for (size_t i = 0; i < pending.size(); ++i) {
+      Pair p = pending[i];
+      if (cudaEventQuery(p.b) != cudaSuccess) { cudaGetLastError(); pending[keep++] = p; continue; }
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+        ms[p.kind] += t;
+        count[p.kind] += 1;
+      } else {
+        cudaGetLastError();
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.resize(keep);
+  }
+  void clear() {
+    resolve();
+    for (int k = 0; k < QS_NUM_TIME_KINDS; ++k) { ms[k] = 0; count[k] = 0; }
+  }
+  ~KernelTimer() {
+    for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+    for (auto e : open) if (e) cudaEventDestroy(e);
+  }
+};
+
+// begin/end on an optional timer
+inline void tbegin(KernelTimer *t, int kind, cudaStream_t s) { if (t) t->begin(kind, s); }
+inline void tend(KernelTimer *t, int kind, cudaStream_t s) { if (t) t->end(kind, s); }
+
 // ------------------------------------------------------------------------
 // Launchers (each returns cudaGetLastError() after the launch).
 // ------------------------------------------------------------------------
@@ -119,6 +183,8 @@ struct Dev {
   uint64_t record_cap;
   int sms;                 // multiprocessor count of the device
   bool wide_offsets;       // 64-bit row offsets in the blocked apply pass at any size
+  bool step_symbolic;      // blocked symbolic pass as one launch per step at any size
+  KernelTimer *timer;      // CUDA-event timing of kernel classes, or nullptr (off)
 };
 
 cudaError_t launch_init(const Dev &d, const uint8_t *initstate_dev, cudaStream_t s);

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <utility>
@@ -127,6 +128,7 @@ struct qs_sim {
   uint32_t flags = 0;
   void *blk = nullptr;  // scratch of the blocked measurement
   bool resumed = false; // state restored by qs_sim_tableau_import: no op log from |0...0>
+  std::unique_ptr<KernelTimer> timer;  // qs_sim_set_timing
 };
 
 namespace {
@@ -166,7 +168,9 @@ int check_usable(qs_sim *s) {
 
 int ensure_cols(qs_sim *s) {
   if (!s->cols_valid) {
+    tbegin(s->d.timer, QS_TIME_TRANSPOSE, s->stream);
     QS_CUDA(s, launch_to_cols(s->d, s->stream));
+    tend(s->d.timer, QS_TIME_TRANSPOSE, s->stream);
     s->launches += 2;
     s->cols_valid = true;
   }
@@ -175,7 +179,9 @@ int ensure_cols(qs_sim *s) {
 
 int ensure_rows(qs_sim *s) {
   if (!s->rows_valid) {
+    tbegin(s->d.timer, QS_TIME_TRANSPOSE, s->stream);
     QS_CUDA(s, launch_to_rows(s->d, s->stream));
+    tend(s->d.timer, QS_TIME_TRANSPOSE, s->stream);
     s->launches += 2;
     s->rows_valid = true;
   }
@@ -282,6 +288,7 @@ int qs_sim_create(uint32_t n, const qs_options *opt, void *cuda_stream, void *wo
   s->stream = static_cast<cudaStream_t>(cuda_stream);
   s->flags = opt ? opt->flags : 0u;
   s->d.wide_offsets = (s->flags & QS_FLAG_WIDE_OFFSETS) != 0;
+  s->d.step_symbolic = (s->flags & QS_FLAG_STEP_SYMBOLIC) != 0;
   if (workspace) {
     if (workspace_bytes < s->plan.total) {
       delete s;
@@ -396,8 +403,10 @@ int qs_sim_apply_layer(qs_sim *s, const qs_gate *gates, uint32_t n_gates) {
   if (!h) return cuda_fail(s, cudaGetLastError(), "staging event");
   memcpy(h, op.packed.data(), op.packed.size() * 4);
   if ((rc = upload(s, slot, op.packed.size() * 4))) return rc;
+  tbegin(s->d.timer, QS_TIME_GATES, s->stream);
   QS_CUDA(s, launch_gate_layer(s->d, reinterpret_cast<const uint32_t *>(s->dstage), n_gates,
                                s->stream));
+  tend(s->d.timer, QS_TIME_GATES, s->stream);
   s->launches += 1;
   s->rows_valid = false;
   s->ops.push_back(std::move(op));
@@ -442,9 +451,11 @@ int qs_sim_apply_layers_dev(qs_sim *s, const uint32_t *packed_dev, const int64_t
     const int64_t cnt = op.ptr[l + 1] - op.ptr[l];
     if (cnt < 0 || cnt > (int64_t)s->d.L.n) return fail(QS_ERR_ARG, "bad layer_ptr");
   }
+  tbegin(s->d.timer, QS_TIME_GATES, s->stream);
   if ((rc = run_dev_layers(s, s->d.X, s->d.Z, s->d.S, s->d.L.cs, packed_dev, op.ptr.data(),
                            op.ptr.size() - 1, true)))
     return rc;
+  tend(s->d.timer, QS_TIME_GATES, s->stream);
   s->rows_valid = false;
   s->ops.push_back(std::move(op));
   return QS_OK;
@@ -461,7 +472,9 @@ static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint6
     while (i < count) {
       if (empty_blocks >= 2) {
         int l = 0;
+        tbegin(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
         QS_CUDA(s, launch_measure_window(s->d, qdev + i, count - i, m0 + i, key, s->stream, &l));
+        tend(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
         s->launches += (uint64_t)l;
         break;
       }
@@ -474,11 +487,14 @@ static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint6
       int32_t done = 0;
       QS_CUDA(s, cudaMemcpyAsync(&done, len_dev, 4, cudaMemcpyDeviceToHost, s->stream));
       QS_CUDA(s, cudaStreamSynchronize(s->stream));
+      if (s->timer) s->timer->resolve();
       if (done < 0 || done > B) return fail(QS_ERR_INTERNAL, "blocked measurement length");
       i += (uint32_t)done;
       if (done < B) {
         l = 0;
+        tbegin(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
         QS_CUDA(s, launch_measure_window(s->d, qdev + i, 1, m0 + i, key, s->stream, &l));
+        tend(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
         s->launches += (uint64_t)l;
         i += 1;
       }
@@ -486,17 +502,19 @@ static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint6
     }
     return QS_OK;
   }
+  tbegin(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
   if (!(s->flags & QS_FLAG_UNPIPELINED_MEASURE) && measure_window_supported(s->d.L)) {
     int l = 0;
     QS_CUDA(s, launch_measure_window(s->d, qdev, count, m0, key, s->stream, &l));
     s->launches += (uint64_t)l;
-    return QS_OK;
+  } else {
+    for (uint32_t i = 0; i < count; ++i) {
+      int l = 0;
+      QS_CUDA(s, launch_measure_one(s->d, qdev, i, m0 + i, key, s->stream, &l));
+      s->launches += (uint64_t)l;
+    }
   }
-  for (uint32_t i = 0; i < count; ++i) {
-    int l = 0;
-    QS_CUDA(s, launch_measure_one(s->d, qdev, i, m0 + i, key, s->stream, &l));
-    s->launches += (uint64_t)l;
-  }
+  tend(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
   return QS_OK;
 }
 
@@ -598,6 +616,36 @@ int qs_sim_noise(qs_sim *s, int kind, double p, const uint32_t *targets, uint32_
 uint64_t qs_sim_num_measurements(const qs_sim *s) { return s ? s->n_meas : 0; }
 
 uint64_t qs_sim_launch_count(const qs_sim *s) { return s ? s->launches : 0; }
+
+int qs_sim_set_timing(qs_sim *s, int on) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  QS_CUDA(s, cudaStreamSynchronize(s->stream));
+  if (!on) {
+    s->d.timer = nullptr;
+    s->timer.reset();
+    return QS_OK;
+  }
+  if (!s->timer) {
+    s->timer.reset(new (std::nothrow) KernelTimer());
+    if (!s->timer) return fail(QS_ERR_OOM, "host allocation failed");
+  }
+  s->timer->clear();
+  s->d.timer = s->timer.get();
+  return QS_OK;
+}
+
+int qs_sim_timing(qs_sim *s, double *ms, uint64_t *count, uint32_t kinds) {
+  if (!s) return fail(QS_ERR_ARG, "sim is NULL");
+  if (!s->timer) return fail(QS_ERR_STATE, "timing is off (qs_sim_set_timing)");
+  QS_CUDA(s, cudaStreamSynchronize(s->stream));
+  s->timer->resolve();
+  for (uint32_t k = 0; k < kinds && k < (uint32_t)QS_NUM_TIME_KINDS; ++k) {
+    if (ms) ms[k] = s->timer->ms[k];
+    if (count) count[k] = s->timer->count[k];
+  }
+  return QS_OK;
+}
 
 int qs_sim_record(qs_sim *s, uint64_t first, uint64_t count, uint8_t *dst) {
   int rc = check_usable(s);
@@ -729,6 +777,7 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
   uint64_t *dout = reinterpret_cast<uint64_t *>(b + c.take((size_t)std::max<uint64_t>(1, M) * ow * 8));
   const bool out_dev = M ? is_device_ptr(record) : true;
   uint64_t *out = out_dev ? record : dout;
+  tbegin(s->d.timer, QS_TIME_SAMPLE, s->stream);
   QS_CUDA(s, launch_frame_init(FX, FZ, n, (uint32_t)fw, seed, s->stream));
   s->launches += 1;
   std::vector<uint32_t> qtmp, seen(n, 0);
@@ -788,6 +837,7 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
       }
     }
   }
+  tend(s->d.timer, QS_TIME_SAMPLE, s->stream);
   if (!out_dev && M)
     QS_CUDA(s, cudaMemcpyAsync(record, dout, (size_t)(M * ow * 8), cudaMemcpyDeviceToHost, s->stream));
   guard.own = false;

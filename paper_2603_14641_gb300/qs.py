@@ -96,6 +96,8 @@ SIGNATURES = {
     "qs_sim_export_rows": (ctypes.c_int, [_vp, _vp, _u32, _vp]),
     "qs_sim_sync": (ctypes.c_int, [_vp]),
     "qs_sim_launch_count": (_u64, [_vp]),
+    "qs_sim_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "qs_sim_timing": (ctypes.c_int, [_vp, _vp, _vp, _u32]),
     "qs_schedule_windows": (ctypes.c_int, [_u32, _vp, _u32, ctypes.c_int, _vp, _vp, _vp,
                                            ctypes.POINTER(_u32)]),
     "qs_schedule_last_error": (ctypes.c_char_p, []),
@@ -152,6 +154,7 @@ QS_FLAG_NO_FUSION = 1
 QS_FLAG_UNPIPELINED_MEASURE = 2
 QS_FLAG_NO_BLOCKED_MEASURE = 4
 QS_FLAG_WIDE_OFFSETS = 8
+QS_FLAG_STEP_SYMBOLIC = 16
 
 
 def qs_sim_required_bytes(n: int, record_capacity: int = 0) -> int:
@@ -316,6 +319,23 @@ def qs_sim_sync(sim: int) -> None:
 
 def qs_sim_launch_count(sim: int) -> int:
     return int(lib().qs_sim_launch_count(ctypes.c_void_p(sim)))
+
+
+QS_TIME_KINDS = ["gates", "transpose", "blk_symbolic", "blk_pivot_rows", "blk_apply", "blk_signs",
+                 "measure_single", "sample"]
+
+
+def qs_sim_set_timing(sim: int, on: bool) -> None:
+    _check(lib().qs_sim_set_timing(ctypes.c_void_p(sim), int(bool(on))), "qs_sim_set_timing")
+
+
+def qs_sim_timing(sim: int) -> dict:
+    """{kind: (milliseconds, timed groups)} for the QS_TIME_* kinds."""
+    k = len(QS_TIME_KINDS)
+    ms = np.zeros(k, np.float64)
+    cnt = np.zeros(k, np.uint64)
+    _check(lib().qs_sim_timing(ctypes.c_void_p(sim), _ptr(ms), _ptr(cnt), k), "qs_sim_timing")
+    return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(QS_TIME_KINDS)}
 
 
 def unpack_rows(buf: np.ndarray, n: int):

@@ -135,6 +135,15 @@ def test_layout_codes_and_native_unpacking():
 def test_option_flags_match_header():
     text = open(HEADER).read()
     for name in ["QS_FLAG_NO_FUSION", "QS_FLAG_UNPIPELINED_MEASURE", "QS_FLAG_NO_BLOCKED_MEASURE",
-                 "QS_FLAG_WIDE_OFFSETS"]:
+                 "QS_FLAG_WIDE_OFFSETS", "QS_FLAG_STEP_SYMBOLIC"]:
         m = re.search(rf"#define\s+{name}\s+(\d+)u", text)
         assert m and int(m.group(1)) == getattr(qs, name), name
+
+
+def test_timing_kinds_match_header():
+    text = open(HEADER).read()
+    names = re.findall(r"\bQS_TIME_([A-Z_]+)\s*=\s*(\d+)", text)
+    assert [int(v) for _, v in names] == list(range(len(names)))
+    assert [nm.lower() for nm, _ in names] == qs.QS_TIME_KINDS
+    m = re.search(r"QS_NUM_TIME_KINDS\s*=\s*(\d+)", text)
+    assert m and int(m.group(1)) == len(qs.QS_TIME_KINDS)

@@ -89,3 +89,33 @@ def test_host_checks_reject_bad_ranges_and_keep_the_sim_usable():
     _, orec, _ = O.run_circuit(circ, seed=5)
     assert np.array_equal(sim.record(), orec)
     assert np.array_equal(sim.record(len(rec) - 3, 3), orec[-3:])
+
+
+def test_kernel_timing_leaves_results_unchanged():
+    """qs_sim_set_timing only timestamps the stream: with timing on, record,
+    tableau and samples equal the oracle's, and every phase that ran (gate
+    layers, layout switch, each part of a blocked measurement block, sampling)
+    has timed groups with positive device time."""
+    circ = C.random_circuit(700, 12, 0.5, seed=12, final_measure_all=True)
+    sim = qs.Simulator(circ.n, device="cuda:0")
+    qs.qs_sim_set_timing(sim.sim, True)
+    dc = sim.upload(circ)
+    rec = sim.run(circ, seed=5, dc=dc)
+    words = sim.sample(64, seed=2, on_device=False)
+    t = qs.qs_sim_timing(sim.sim)
+    o, orec, _ = O.run_circuit(circ, seed=5)
+    assert np.array_equal(rec, orec)
+    x, z, r = sim.export()
+    ox, oz, orr = o.get()
+    assert np.array_equal(x, ox) and np.array_equal(z, oz) and np.array_equal(r, orr)
+    bits = np.unpackbits(words.view(np.uint8), axis=1, bitorder="little")
+    assert np.array_equal(bits, O.frames(circ, orec, 64, seed=2))
+    for kind in ("gates", "transpose", "blk_symbolic", "blk_pivot_rows", "blk_apply", "blk_signs",
+                 "sample"):
+        ms, cnt = t[kind]
+        assert cnt > 0 and ms > 0, (kind, t[kind])
+    assert t["blk_apply"][1] >= 5
+    qs.qs_sim_set_timing(sim.sim, False)
+    with pytest.raises(qs.QsError):
+        qs.qs_sim_timing(sim.sim)
+    sim.sync()

@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import oracle as O  # noqa: E402
+from tests import oracle_jobs  # noqa: E402
 from paper_2603_14641_gb300 import qs  # noqa: E402
 from workloads import circuits as C  # noqa: E402
 
@@ -282,25 +283,62 @@ def test_full_180k_measure_twice_and_inverse():
     sim2.sync()
 
 
+def _assert_against_job(name, sim, rec):
+    """GPU record, kinds and whole tableau against an oracle job's result."""
+    want = oracle_jobs.result(name)
+    assert int(want["odd"]) == 0 and int(want["det_fail"]) == 0
+    assert np.array_equal(rec, want["rec"]), "records differ"
+    assert np.array_equal(sim.record_kinds(), want["kinds"]), "kinds differ"
+    x, z, r = sim.export()
+    assert np.array_equal(np.packbits(x, axis=1), want["x"]), "x bits differ"
+    assert np.array_equal(np.packbits(z, axis=1), want["z"]), "z bits differ"
+    assert np.array_equal(r, want["r"]), "signs differ"
+    return want
+
+
+def _run_job_program(name):
+    prog = oracle_jobs.program(name)
+    sim = _sim(prog.n)
+    dc = sim.upload(prog)
+    rec = sim.run(prog, seed=oracle_jobs.SEEDS[name], dc=dc)
+    return sim, rec
+
+
 @pytest.mark.slow
 def test_oracle_parity_on_a_20k_prefix_of_the_180k_workload():
     """The 180,000-qubit workload's generator (p_cx 0.4, seed 3) at 20,000
     qubits: its first two layers, then the first 64 of the final all-qubit
     measurement (blocked, with deterministic steps in between), against the
     oracle: record, kinds and the whole tableau."""
-    n = 20_000
-    circ = C.workload_180k_prefix(n, depth=2)
-    q = np.arange(64, dtype=np.uint32)
-    prog = C.Circuit(n=n, gates=circ.gates, layer_ptr=circ.layer_ptr,
-                     ops=[("layers", 0, 2), ("measure", q)])
-    sim = _sim(n)
-    dc = sim.upload(prog)
-    rec = sim.run(prog, seed=7, dc=dc)
-    o, orec, okinds = O.run_circuit(prog, seed=7)
-    assert 0 < int(okinds.sum()) < len(q)  # both kinds occur
-    assert np.array_equal(rec, orec)
-    assert np.array_equal(sim.record_kinds(), okinds)
-    _assert_tableau(sim, o)
+    sim, rec = _run_job_program("prefix_180k_20k")
+    want = _assert_against_job("prefix_180k_20k", sim, rec)
+    assert 0 < int(want["kinds"].sum()) < len(rec)  # both kinds occur
+    sim.sync()
+
+
+@pytest.mark.slow
+def test_oracle_parity_above_the_one_cta_symbolic_limit():
+    """The 180,000-qubit workload's generator (p_cx 0.4, seed 3) at 30,000
+    qubits, above the 25,600 qubits up to which one CTA runs the symbolic
+    pass: the blocked measurement takes the per-step symbolic launches (the
+    path of every measurement block at 180,000 qubits) with no flag. Two
+    layers, then the first 64 of the final all-qubit measurement, against the
+    oracle: record, kinds and the whole tableau."""
+    sim, rec = _run_job_program("prefix_180k_30k")
+    want = _assert_against_job("prefix_180k_30k", sim, rec)
+    assert 0 < int(want["kinds"].sum()) < len(rec)
+    sim.sync()
+
+
+@pytest.mark.slow
+def test_10k_schedule_prefix_matches_oracle():
+    """The 10,000-qubit workload at full size: layers 0-100 with its two
+    windows of 500 mid-circuit measurements (fused gate segments, blocked
+    measurement windows), then the first 256 of its final all-qubit round,
+    against the oracle: record, kinds and the whole tableau."""
+    sim, rec = _run_job_program("schedule_10k")
+    want = _assert_against_job("schedule_10k", sim, rec)
+    assert len(rec) == 1256 and int(want["kinds"].sum()) > 900
     sim.sync()
 
 
@@ -364,17 +402,20 @@ def test_pipelined_measurements_match_five_launch_path(n):
         assert np.array_equal(outs[0][0], orec)
 
 
+@pytest.mark.parametrize("flags", [0, qs.QS_FLAG_STEP_SYMBOLIC], ids=["one-cta-symbolic", "step-symbolic"])
 @pytest.mark.parametrize("n,count", [(64, 16), (65, 64), (256, 256), (300, 100), (1024, 16),
                                      (1100, 200), (2000, 150), (4097, 70)])
-def test_blocked_measurement_matches_oracle(n, count):
+def test_blocked_measurement_matches_oracle(n, count, flags):
     """Windows of >= 16 measurements on >= 64 qubits go through the blocked
     path (up to 64 measurements per tableau pass); repeated qubits force
-    deterministic outcomes that end a block early."""
+    deterministic outcomes that end a block early. QS_FLAG_STEP_SYMBOLIC runs
+    the symbolic pass as one launch per step over every row, the code path
+    that tableaus above 25,600 qubits (the 180,000-qubit workload) take."""
     circ = C.random_circuit(n, 12, 0.5, seed=n + count, final_measure_all=False)
     rng = np.random.default_rng(count)
     q = rng.permutation(n)[:count].astype(np.uint32)
     q = np.concatenate([q[: count // 2], q[: 7], q[count // 2:]])  # repeats inside the window
-    sim = _sim(n)
+    sim = _sim(n, flags=flags)
     dc = sim.upload(circ)
     sim.apply_layers_dev(dc, 0, circ.n_layers)
     rec = sim.measure(q, seed=23, shot=1)
@@ -399,7 +440,7 @@ def test_wide_offset_apply_pass_matches_oracle(n, count):
     o = O.Oracle(n)
     o.apply(circ.gates)
     orec, _ = o.measure(q, seed=6)
-    for flags in (qs.QS_FLAG_WIDE_OFFSETS, 0):
+    for flags in (qs.QS_FLAG_WIDE_OFFSETS, 0, qs.QS_FLAG_WIDE_OFFSETS | qs.QS_FLAG_STEP_SYMBOLIC):
         sim = _sim(n, flags=flags)
         dc = sim.upload(circ)
         sim.apply_layers_dev(dc, 0, circ.n_layers)

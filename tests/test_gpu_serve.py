@@ -1,12 +1,14 @@
 """GPU test of the serving loop: requests admitted while others run overlap on
 the device, and every request's single-shot record and frame samples are
-bit-identical to the same request served alone."""
+bit-identical to the same request served alone and to the oracle (CHP record
+and Pauli-frame samples of Sec. 2.5 and Sec. 5 under the same keys)."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import oracle as O  # noqa: E402
 from paper_2603_14641_gb300 import serve  # noqa: E402
 from workloads import circuits as C  # noqa: E402
 
@@ -35,6 +37,14 @@ def test_results_identical_alone_and_in_the_mix():
         a, m = alone[0], mixed[r.rid]
         assert np.array_equal(a.record, m.record), f"request {r.rid}: record differs"
         assert np.array_equal(a.samples, m.samples), f"request {r.rid}: samples differ"
+        # the served request against the oracle under the same keys: the
+        # record is measured with key (seed, 0), the shots with seed + 1
+        _, orec, _ = O.run_circuit(r.circuit, seed=r.seed, shot=0)
+        assert np.array_equal(m.record, orec), f"request {r.rid}: record differs from the oracle"
+        bits = np.unpackbits(m.samples.view(np.uint8), axis=1, bitorder="little")
+        assert not bits[:, r.shots:].any()
+        want = O.frames(r.circuit, orec, r.shots, seed=r.seed + 1)
+        assert np.array_equal(bits[:, :r.shots], want), f"request {r.rid}: samples differ from the oracle"
 
 
 def test_tight_budget_serialises_but_completes():
