@@ -101,6 +101,20 @@ typedef struct qs_options {
  * shared memory. The flag runs the large-size code path at any size
  * (identical results). */
 #define QS_FLAG_STEP_SYMBOLIC 16u
+/* qs_options.flags: inverse-tableau mode, the representation of the paper's
+ * own measurement variant (Sec. 3.2, Alg. 1: Gaussian elimination by CX
+ * injection, as in Stim). For the Clifford C that prepares the state from
+ * |0...0>, the sim keeps C^dag Z_q C and C^dag X_q C with qubit-indexed
+ * signs S_S[q] and S_D[q] (qs_sim_qubit_signs). The tableau bits are those
+ * of the default (CHP) mode under gates, read by columns; per-row signs are
+ * not kept (exports give 0 there). Measurements run Alg. 1 (pivot = smallest
+ * anticommuting stabilizer, CX injections into the later ones, an H or H_YZ
+ * and an X injection on the pivot), four launches each; records and
+ * measurement kinds equal the CHP mode's under the same keys, and the state
+ * is the same, though the tableau bits after a measurement differ. Layers
+ * run one launch each (no fused segments); measurements are never blocked;
+ * qs_sim_tableau_import is refused. Fixed at create. */
+#define QS_FLAG_INVERSE_TABLEAU 32u
 
 typedef struct qs_sim qs_sim;
 
@@ -314,6 +328,16 @@ int qs_sim_tableau_import(qs_sim *sim, int layout, const void *src, size_t src_b
  * Errors: QS_ERR_ARG (row >= 2n or NULL pointers).
  */
 int qs_sim_export_rows(qs_sim *sim, const uint32_t *rows, uint32_t count, uint64_t *dst);
+
+/*
+ * Inverse-tableau mode only (QS_FLAG_INVERSE_TABLEAU): copies the qubit-indexed
+ * signs of Alg. 1 to dst (host or device): ceil(n/64) words of S_S (bit q of
+ * word q / 64 = sign of C^dag Z_q C), then ceil(n/64) words of S_D (sign of
+ * C^dag X_q C). dst_words >= 2 ceil(n/64). Syncs.
+ * Errors: QS_ERR_ARG (NULL dst), QS_ERR_SIZE, QS_ERR_STATE (the sim is in
+ * the default mode).
+ */
+int qs_sim_qubit_signs(qs_sim *sim, uint64_t *dst, size_t dst_words);
 
 /* Waits for the stream and checks the device error flags:
  * QS_ERR_INTERNAL if a self-check failed, QS_ERR_TIMEOUT if a bounded wait

@@ -28,6 +28,7 @@ namespace qs {
 
 constexpr int kDetBlocks = 152;     // chunks of the deterministic product (one per SM)
 constexpr int kMeasStateWords = 16; // per-measurement device state
+constexpr int kInvChunks = 256;     // row chunks of the inverse-mode target pass
 
 // device error flags (sticky, cleared by reset)
 enum : uint32_t {
@@ -185,6 +186,9 @@ struct Dev {
   bool wide_offsets;       // 64-bit row offsets in the blocked apply pass at any size
   bool step_symbolic;      // blocked symbolic pass as one launch per step at any size
   KernelTimer *timer;      // CUDA-event timing of kernel classes, or nullptr (off)
+  bool inverse;            // inverse-tableau mode (qubit-indexed signs, Alg. 1 measurement)
+  uint64_t *qsig;          // inverse mode: S_S then S_D, rs words each
+  uint64_t *inv_part;      // inverse mode: measurement partials, 6 * kInvChunks * rs words
 };
 
 cudaError_t launch_init(const Dev &d, const uint8_t *initstate_dev, cudaStream_t s);
@@ -212,6 +216,14 @@ cudaError_t launch_frame_noise(uint64_t *FX, uint64_t *FZ, uint32_t fw, uint32_t
                                const uint32_t *targets, uint32_t count, uint32_t i0, int kind,
                                uint64_t thr, uint64_t e, uint64_t seed, cudaStream_t s);
 cudaError_t launch_reset_meas_state(const Dev &d, cudaStream_t s);
+// column q = qubits[i] of the row-major x part into colx, pivot by atomicMin into mst
+cudaError_t launch_gather(const Dev &d, const uint32_t *qubits, uint32_t i, cudaStream_t s);
+// inverse-tableau mode (qs_inverse.cu)
+cudaError_t launch_inv_init_signs(const Dev &d, const uint8_t *initstate_dev, cudaStream_t s);
+cudaError_t launch_inv_gate_layer(const Dev &d, const uint32_t *packed, uint32_t n_gates, cudaStream_t s);
+size_t inv_scratch_words(const Layout &L);
+cudaError_t launch_inv_measure_one(const Dev &d, const uint32_t *qubits, uint32_t i, uint64_t midx,
+                                   qs_key key, cudaStream_t s, int *launches);
 // a window of measurements qubits[0..count) with record indices m0.., two
 // launches per measurement (plus two per window)
 bool measure_window_supported(const Layout &L);

@@ -286,6 +286,13 @@ finalize_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t r
 
 static std::atomic<uint64_t> g_rowsum_attr_set{0};
 
+cudaError_t launch_gather(const Dev &d, const uint32_t *qubits, uint32_t i, cudaStream_t s) {
+  const Layout &L = d.L;
+  gather_kernel<<<(uint32_t)((L.nrows + 255) / 256), 256, 0, s>>>(d.RX, L.rs, L.nrows, L.n, L.k, qubits,
+                                                                 i, d.colx, d.mst, d.err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_measure_one(const Dev &d, const uint32_t *qubits, uint32_t i, uint64_t midx,
                                qs_key key, cudaStream_t s, int *launches) {
   const Layout &L = d.L;

@@ -72,7 +72,7 @@ struct Carve {
 };
 
 struct Plan {
-  size_t X, Z, RX, RZ, S, colx, mst, detx, detz, dets, err, record, kinds, stage, blk, total;
+  size_t X, Z, RX, RZ, S, colx, mst, detx, detz, dets, err, record, kinds, stage, blk, qsig, invp, total;
   uint64_t record_cap;
   size_t stage_bytes;
 };
@@ -98,6 +98,9 @@ Plan make_plan(const Layout &L, const qs_options *opt) {
   p.kinds = c.take(p.record_cap);
   p.stage = c.take(p.stage_bytes);
   p.blk = c.take(blocked_scratch_bytes(L));
+  const bool inverse = opt && (opt->flags & QS_FLAG_INVERSE_TABLEAU);
+  p.qsig = c.take(inverse ? 2ull * L.rs * 8 : 0);
+  p.invp = c.take(inverse ? inv_scratch_words(L) * 8 : 0);
   p.total = c.off;
   return p;
 }
@@ -231,7 +234,7 @@ int run_dev_layers(qs_sim *s, uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t st
                    const uint32_t *packed, const int64_t *ptr, size_t nlayers, bool tableau) {
   const uint32_t n = s->d.L.n;
   if (nlayers == 0) return QS_OK;
-  if (fused_fits(n) && !(s->flags & QS_FLAG_NO_FUSION)) {
+  if (fused_fits(n) && !(s->flags & QS_FLAG_NO_FUSION) && !(tableau && s->d.inverse)) {
     const size_t cap = s->plan.stage_bytes / 8 - 1;  // layers per staged offset table
     for (size_t l0 = 0; l0 < nlayers; l0 += cap) {
       const size_t L = std::min(cap, nlayers - l0);
@@ -251,7 +254,9 @@ int run_dev_layers(qs_sim *s, uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t st
   for (size_t l = 0; l < nlayers; ++l) {
     const int64_t a = ptr[l], cnt = ptr[l + 1] - a;
     if (cnt == 0) continue;
-    if (tableau)
+    if (tableau && s->d.inverse)
+      QS_CUDA(s, launch_inv_gate_layer(s->d, packed + 2 * a, (uint32_t)cnt, s->stream));
+    else if (tableau)
       QS_CUDA(s, launch_gate_layer(s->d, packed + 2 * a, (uint32_t)cnt, s->stream));
     else
       QS_CUDA(s, launch_frame_layer(X, Z, n, stride, packed + 2 * a, (uint32_t)cnt, s->d.err,
@@ -289,6 +294,7 @@ int qs_sim_create(uint32_t n, const qs_options *opt, void *cuda_stream, void *wo
   s->flags = opt ? opt->flags : 0u;
   s->d.wide_offsets = (s->flags & QS_FLAG_WIDE_OFFSETS) != 0;
   s->d.step_symbolic = (s->flags & QS_FLAG_STEP_SYMBOLIC) != 0;
+  s->d.inverse = (s->flags & QS_FLAG_INVERSE_TABLEAU) != 0;
   if (workspace) {
     if (workspace_bytes < s->plan.total) {
       delete s;
@@ -323,6 +329,8 @@ int qs_sim_create(uint32_t n, const qs_options *opt, void *cuda_stream, void *wo
   s->d.record_cap = p.record_cap;
   s->dstage = b + p.stage;
   s->blk = b + p.blk;
+  s->d.qsig = s->d.inverse ? reinterpret_cast<uint64_t *>(b + p.qsig) : nullptr;
+  s->d.inv_part = s->d.inverse ? reinterpret_cast<uint64_t *>(b + p.invp) : nullptr;
   int dev = 0;
   cudaGetDevice(&dev);
   s->d.sms = 152;
@@ -372,7 +380,14 @@ int qs_sim_reset(qs_sim *s, const uint8_t *initstate) {
     init_dev = s->dstage;
   }
   QS_CUDA(s, cudaMemsetAsync(s->d.err, 0, 4, s->stream));
-  QS_CUDA(s, launch_init(s->d, init_dev, s->stream));
+  if (s->d.inverse) {
+    // same bits as the CHP mode, no per-row signs; the basis state sits in S_S
+    QS_CUDA(s, launch_init(s->d, nullptr, s->stream));
+    QS_CUDA(s, launch_inv_init_signs(s->d, init_dev, s->stream));
+    s->launches += 1;
+  } else {
+    QS_CUDA(s, launch_init(s->d, init_dev, s->stream));
+  }
   QS_CUDA(s, launch_reset_meas_state(s->d, s->stream));
   s->launches += 3;
   s->cols_valid = true;
@@ -404,8 +419,12 @@ int qs_sim_apply_layer(qs_sim *s, const qs_gate *gates, uint32_t n_gates) {
   memcpy(h, op.packed.data(), op.packed.size() * 4);
   if ((rc = upload(s, slot, op.packed.size() * 4))) return rc;
   tbegin(s->d.timer, QS_TIME_GATES, s->stream);
-  QS_CUDA(s, launch_gate_layer(s->d, reinterpret_cast<const uint32_t *>(s->dstage), n_gates,
-                               s->stream));
+  if (s->d.inverse)
+    QS_CUDA(s, launch_inv_gate_layer(s->d, reinterpret_cast<const uint32_t *>(s->dstage), n_gates,
+                                     s->stream));
+  else
+    QS_CUDA(s, launch_gate_layer(s->d, reinterpret_cast<const uint32_t *>(s->dstage), n_gates,
+                                 s->stream));
   tend(s->d.timer, QS_TIME_GATES, s->stream);
   s->launches += 1;
   s->rows_valid = false;
@@ -462,6 +481,16 @@ int qs_sim_apply_layers_dev(qs_sim *s, const uint32_t *packed_dev, const int64_t
 }
 
 static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint64_t m0, qs_key key) {
+  if (s->d.inverse) {  // Alg. 1, one measurement after another
+    tbegin(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
+    for (uint32_t i = 0; i < count; ++i) {
+      int l = 0;
+      QS_CUDA(s, launch_inv_measure_one(s->d, qdev, i, m0 + i, key, s->stream, &l));
+      s->launches += (uint64_t)l;
+    }
+    tend(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
+    return QS_OK;
+  }
   if (!(s->flags & (QS_FLAG_UNPIPELINED_MEASURE | QS_FLAG_NO_BLOCKED_MEASURE)) &&
       measure_window_supported(s->d.L) && count >= kBlockedMinCount && s->d.L.n >= kBlockedMinQubits) {
     // blocks of up to 64 measurements; a block stops before a deterministic
@@ -916,6 +945,7 @@ int qs_sim_tableau_import(qs_sim *s, int layout, const void *src, size_t src_byt
   Range range_("qs_sim_tableau_import");
   int rc = check_usable(s);
   if (rc) return rc;
+  if (s->d.inverse) return fail(QS_ERR_ARG, "qs_sim_tableau_import is not supported in inverse-tableau mode");
   if (layout != QS_LAYOUT_ROWS_PACKED && layout != QS_LAYOUT_NATIVE)
     return fail(QS_ERR_ARG, "unknown layout");
   const Layout &L = s->d.L;
@@ -985,6 +1015,19 @@ int qs_sim_tableau_import(qs_sim *s, int layout, const void *src, size_t src_byt
   s->ops.clear();
   s->resumed = true;
   return QS_OK;
+}
+
+int qs_sim_qubit_signs(qs_sim *s, uint64_t *dst, size_t dst_words) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (!s->d.inverse) return fail(QS_ERR_STATE, "qubit signs exist in inverse-tableau mode only");
+  if (!dst) return fail(QS_ERR_ARG, "dst is NULL");
+  const size_t w = s->d.L.k;  // ceil(n / 64)
+  if (dst_words < 2 * w) return fail(QS_ERR_SIZE, "dst smaller than 2 ceil(n/64) words");
+  const cudaMemcpyKind kind = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  QS_CUDA(s, cudaMemcpyAsync(dst, s->d.qsig, w * 8, kind, s->stream));
+  QS_CUDA(s, cudaMemcpyAsync(dst + w, s->d.qsig + s->d.L.rs, w * 8, kind, s->stream));
+  return qs_sim_sync(s);
 }
 
 int qs_sim_export_rows(qs_sim *s, const uint32_t *rows, uint32_t count, uint64_t *dst) {

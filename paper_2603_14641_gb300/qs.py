@@ -97,6 +97,7 @@ SIGNATURES = {
     "qs_sim_sync": (ctypes.c_int, [_vp]),
     "qs_sim_launch_count": (_u64, [_vp]),
     "qs_sim_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "qs_sim_qubit_signs": (ctypes.c_int, [_vp, _vp, _sz]),
     "qs_sim_timing": (ctypes.c_int, [_vp, _vp, _vp, _u32]),
     "qs_schedule_windows": (ctypes.c_int, [_u32, _vp, _u32, ctypes.c_int, _vp, _vp, _vp,
                                            ctypes.POINTER(_u32)]),
@@ -155,10 +156,11 @@ QS_FLAG_UNPIPELINED_MEASURE = 2
 QS_FLAG_NO_BLOCKED_MEASURE = 4
 QS_FLAG_WIDE_OFFSETS = 8
 QS_FLAG_STEP_SYMBOLIC = 16
+QS_FLAG_INVERSE_TABLEAU = 32
 
 
-def qs_sim_required_bytes(n: int, record_capacity: int = 0) -> int:
-    opt = qs_options(record_capacity, 0, 0)
+def qs_sim_required_bytes(n: int, record_capacity: int = 0, flags: int = 0) -> int:
+    opt = qs_options(record_capacity, flags, 0)
     return int(lib().qs_sim_required_bytes(n, ctypes.byref(opt)))
 
 
@@ -325,6 +327,16 @@ QS_TIME_KINDS = ["gates", "transpose", "blk_symbolic", "blk_pivot_rows", "blk_ap
                  "measure_single", "sample"]
 
 
+def qs_sim_qubit_signs(sim: int, n: int):
+    """Inverse-tableau mode: (S_S, S_D) as uint8 arrays of n bits (signs of
+    C^dag Z_q C and C^dag X_q C)."""
+    w = (n + 63) // 64
+    buf = np.zeros(2 * w, np.uint64)
+    _check(lib().qs_sim_qubit_signs(ctypes.c_void_p(sim), _ptr(buf), 2 * w), "qs_sim_qubit_signs")
+    bits = np.unpackbits(buf.view(np.uint8), bitorder="little")
+    return bits[:n].copy(), bits[64 * w:64 * w + n].copy()
+
+
 def qs_sim_set_timing(sim: int, on: bool) -> None:
     _check(lib().qs_sim_set_timing(ctypes.c_void_p(sim), int(bool(on))), "qs_sim_set_timing")
 
@@ -385,7 +397,8 @@ class Simulator:
         self.n = int(n)
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        nbytes = qs_sim_required_bytes(self.n, record_capacity)
+        nbytes = qs_sim_required_bytes(self.n, record_capacity, flags)
+        self.flags = flags
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.sim = qs_sim_create(self.n, self.stream.cuda_stream, self.workspace.data_ptr(), nbytes,
                                  record_capacity, flags)
@@ -455,6 +468,10 @@ class Simulator:
     @property
     def num_measurements(self) -> int:
         return qs_sim_num_measurements(self.sim)
+
+    def qubit_signs(self):
+        """Inverse-tableau mode: (S_S, S_D) uint8 arrays of n bits."""
+        return qs_sim_qubit_signs(self.sim, self.n)
 
     def record(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
         return qs_sim_record(self.sim, first, count)
