@@ -400,23 +400,37 @@ struct ApplyRow {
   uint2 x, z;       // this lane's word of x and z, as 32-bit halves
 };
 
-// Idx: 32-bit offsets when the row-major matrix has fewer than 2^32 words
-template <typename Idx>
-__device__ __forceinline__ void apply_fetch(ApplyRow &a, uint32_t r, uint32_t nrows, const uint64_t *RX,
-                                            const uint64_t *RZ, Idx off, bool ok, const uint64_t *M,
-                                            const int32_t *base) {
-  a.b = kBaseOrig;
-  a.lo = a.hi = 0;
-  a.x = a.z = make_uint2(0, 0);
+// pattern M_r and base_r of a row (one stage ahead of its words)
+struct ApplyMeta {
+  int32_t b;
+  uint32_t lo, hi;
+};
+
+__device__ __forceinline__ void apply_meta(ApplyMeta &m, uint32_t r, uint32_t nrows, const uint64_t *M,
+                                           const int32_t *base) {
+  m.b = kBaseOrig;
+  m.lo = m.hi = 0;
   if (r < nrows) {
-    a.b = __ldg(base + r);
-    const uint2 m = __ldg(reinterpret_cast<const uint2 *>(M) + r);
-    a.lo = m.x;
-    a.hi = m.y;
-    if (ok) {
-      a.x = reinterpret_cast<const uint2 *>(RX)[off];
-      a.z = reinterpret_cast<const uint2 *>(RZ)[off];
-    }
+    m.b = __ldg(base + r);
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(M) + r);
+    m.lo = v.x;
+    m.hi = v.y;
+  }
+}
+
+// the row's words, fetched only when the row changes: a row that no step
+// targeted and that kept its original base (M_r = 0, base_r original; e.g.
+// the +-Z_q pivot rows of earlier blocks) is neither read nor written
+template <typename Idx>
+__device__ __forceinline__ void apply_fetch(ApplyRow &a, const ApplyMeta &m, const uint64_t *RX,
+                                            const uint64_t *RZ, Idx off, bool ok) {
+  a.b = m.b;
+  a.lo = m.lo;
+  a.hi = m.hi;
+  a.x = a.z = make_uint2(0, 0);
+  if (ok && (m.b != kBaseOrig || (m.lo | m.hi) != 0)) {
+    a.x = reinterpret_cast<const uint2 *>(RX)[off];
+    a.z = reinterpret_cast<const uint2 *>(RZ)[off];
   }
 }
 
@@ -543,17 +557,25 @@ blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t 
   const uint64_t tp0 = (uint64_t)blockIdx.x * nrows;
   uint32_t r = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
   Idx off = (Idx)r * rs + word;
-  // unrolled by three so the rows in flight rotate through registers without copies
+  // unrolled by three so the rows in flight rotate through registers without
+  // copies; each row's pattern is loaded one stage before its words
   ApplyRow a0, a1, a2;
-  apply_fetch<Idx>(a0, r, nrows, RX, RZ, off, ok, M, base);
-  apply_fetch<Idx>(a1, r + units, nrows, RX, RZ, off + step, ok, M, base);
+  ApplyMeta mn;
+  apply_meta(mn, r, nrows, M, base);
+  apply_fetch<Idx>(a0, mn, RX, RZ, off, ok);
+  apply_meta(mn, r + units, nrows, M, base);
+  apply_fetch<Idx>(a1, mn, RX, RZ, off + step, ok);
+  apply_meta(mn, r + 2 * units, nrows, M, base);
   for (; r < nrows; r += 3 * units, off += 3 * step) {
-    apply_fetch<Idx>(a2, r + 2 * units, nrows, RX, RZ, off + 2 * step, ok, M, base);
+    apply_fetch<Idx>(a2, mn, RX, RZ, off + 2 * step, ok);
+    apply_meta(mn, r + 3 * units, nrows, M, base);
     apply_row<Idx>(a0, r, nrows, RX, RZ, off, ok, word, qubits, VX, VZ, rs, lane, tl, Tp, tp0);
-    apply_fetch<Idx>(a0, r + 3 * units, nrows, RX, RZ, off + 3 * step, ok, M, base);
+    apply_fetch<Idx>(a0, mn, RX, RZ, off + 3 * step, ok);
+    apply_meta(mn, r + 4 * units, nrows, M, base);
     apply_row<Idx>(a1, r + units, nrows, RX, RZ, off + step, ok, word, qubits, VX, VZ, rs, lane, tl, Tp,
                    tp0);
-    apply_fetch<Idx>(a1, r + 4 * units, nrows, RX, RZ, off + 4 * step, ok, M, base);
+    apply_fetch<Idx>(a1, mn, RX, RZ, off + 4 * step, ok);
+    apply_meta(mn, r + 5 * units, nrows, M, base);
     apply_row<Idx>(a2, r + 2 * units, nrows, RX, RZ, off + 2 * step, ok, word, qubits, VX, VZ, rs, lane,
                    tl, Tp, tp0);
   }
