@@ -812,6 +812,47 @@ def serve_cpu_baseline(specs, circs, shots: int = 20000):
                       f"frame shots, {dt:.1f} s of CPU"}
 
 
+def run_l2probe(args):
+    """Evidence for the fused-depth question at 180k qubits (L2-resident slabs):
+    the in-place read-modify-write rate of a buffer that fits L2 against one
+    that does not. A slab of generator words evolved through many layers in L2
+    moves each layer's column words through L2 instead of HBM, so fusing can
+    save at most 1 - (HBM rate / L2 rate) of the gate phase, before the grid-wide
+    barrier every layer would need. Timed with CUDA events over back-to-back
+    in-place XORs of int64 buffers (torch elementwise kernels; a probe of the
+    memory system, not of this library's kernels)."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    out = {}
+    for mb in (16, 32, 64, 96, 8192):
+        n = mb * (1 << 20) // 8
+        a = torch.randint(-2**62, 2**62, (n,), dtype=torch.int64, device=dev)
+        b = torch.randint(-2**62, 2**62, (n,), dtype=torch.int64, device=dev)
+        reps = max(3, int(4096 // mb))
+        for _ in range(3):
+            a.bitwise_xor_(b)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            a.bitwise_xor_(b)
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / reps
+        # bytes: read a and b, write a
+        out[f"{mb}MB"] = {"ms": ms, "tb_per_s": 3 * n * 8 / (ms / 1e3) / 1e12, "reps": reps}
+        del a, b
+    hbm = out["8192MB"]["tb_per_s"]
+    l2 = max(out[k]["tb_per_s"] for k in ("16MB", "32MB", "64MB"))
+    res = {"metric": "in-place read-modify-write rate, L2-resident vs HBM-resident buffers",
+           "unit": "TB/s", "rates": out, "l2_over_hbm": l2 / hbm,
+           "max_gate_phase_saving_from_l2_slabs": 1 - hbm / l2,
+           "note": "upper bound on what fused depth through L2-resident slabs can save in the "
+                   "180k gate phase (before per-layer grid barriers)"}
+    print(json.dumps(res))
+
+
 def run_reference(args):
     """The oracle as it stands on one host core, for the same metric: each step
     evolves `cpu_rows` sampled generator rows of the 180k workload's circuit
@@ -861,7 +902,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n180k", choices=sorted(WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="n180k",
+                    choices=sorted(WORKLOADS) + ["batch", "serve", "l2probe"])
     ap.add_argument("--serve-count", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=int, default=96)
@@ -893,6 +935,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "l2probe":
+        run_l2probe(args)
     else:
         run_ours(args)
 
