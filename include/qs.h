@@ -359,13 +359,19 @@ int qs_sim_sync(qs_sim *sim);
  *   - 2 * n * ceil(ceil(shots/64)/4)*4 * 8 bytes of frames (each rounded up to
  *     256) plus M * ceil(shots/64) * 8 bytes must fit in the array, else
  *     QS_ERR_SIZE with the sizes in qs_last_error().
- *   - Every GPU that loads libqs holds the array until the process exits.
+ *   - The array is placed on a device, and its address looked up, when the
+ *     first sim is created there (qs_sim_create, with that device current), so a
+ *     process that creates its sims before it reserves the rest of the GPU for
+ *     its own pool has the array in place; from then on that GPU holds it until
+ *     the process exits. If that set-up failed at create (the sim itself is
+ *     fine), the first qs_sim_sample_noalloc on the device tries again and, if it
+ *     fails, returns QS_ERR_CUDA without marking the sim unusable.
  *   - All calls share the array and each call starts by clearing it (X~ = 0,
  *     Z~ rewritten); two calls whose work overlaps on the GPU (different
  *     streams, or different sims on one device) race on it. Calls from several
  *     host threads are serialised on the host, not on the GPU.
- *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *   - When the set-up is left to the first qs_sim_sample_noalloc on a device
+ *     (create could not do it), make that first call before any stream capture.
  */
 #define QS_NOALLOC_SCRATCH_BYTES (32u << 20)
 int qs_sim_sample_noalloc(qs_sim *sim, uint64_t shots, uint64_t seed, uint64_t *record,

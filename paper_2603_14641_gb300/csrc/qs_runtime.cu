@@ -268,6 +268,10 @@ int run_dev_layers(qs_sim *s, uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t st
 
 }  // namespace
 
+// device address of the allocation-free sampler's static array on the current
+// device (looked up once per device; defined with the array further below)
+static cudaError_t noalloc_setup(void **addr);
+
 extern "C" {
 
 const char *qs_version(void) { return "qs-gb300 0.1 (sm_103a)"; }
@@ -333,6 +337,13 @@ int qs_sim_create(uint32_t n, const qs_options *opt, void *cuda_stream, void *wo
   s->d.inv_part = s->d.inverse ? reinterpret_cast<uint64_t *>(b + p.invp) : nullptr;
   int dev = 0;
   cudaGetDevice(&dev);
+  {
+    // place the allocation-free sampler's array on this device now, before the
+    // caller may reserve the rest of the GPU; a failure here only matters to
+    // qs_sim_sample_noalloc, which retries and reports it
+    void *unused = nullptr;
+    if (noalloc_setup(&unused) != cudaSuccess) cudaGetLastError();
+  }
   s->d.sms = 152;
   cudaDeviceGetAttribute(&s->d.sms, cudaDevAttrMultiProcessorCount, dev);
   for (int i = 0; i < kRing; ++i) {
@@ -1083,6 +1094,30 @@ void *g_noalloc_addr[kNoallocMaxDevices] = {};
 uint64_t g_noalloc_seen[(kMaxQubits + 63) / 64];
 }  // namespace
 
+// Set-up, once per device with that device current: the host-side name of the
+// array is not a device address, so ask the runtime for it (this also loads
+// the array onto the device). Callers hold g_noalloc_mu or are qs_sim_create.
+static cudaError_t noalloc_setup_locked(void **addr) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_frames);
+    if (e != cudaSuccess) return e;
+    if (!p) return cudaErrorInvalidSymbol;
+    g_noalloc_addr[dev] = p;
+  }
+  *addr = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+static cudaError_t noalloc_setup(void **addr) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  return noalloc_setup_locked(addr);
+}
+
 extern "C" int qs_sim_sample_noalloc(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record,
                                      size_t record_words) {
   Range range_("qs_sim_sample_noalloc");
@@ -1111,15 +1146,17 @@ extern "C" int qs_sim_sample_noalloc(qs_sim *s, uint64_t shots, uint64_t seed, u
   QS_CUDA(s, cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoallocMaxDevices) return fail(QS_ERR_ARG, "device ordinal too large");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    // set-up, once per device with that device current: the host-side name of
-    // the array is not a device address, so ask the runtime for it
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_frames);
-    if (e != cudaSuccess || !p) return cuda_fail(s, e, "cudaGetSymbolAddress(g_noalloc_frames)");
-    g_noalloc_addr[dev] = p;
+  void *addr = nullptr;
+  {
+    // normally done at qs_sim_create; a failure here leaves the sim usable
+    cudaError_t e = noalloc_setup_locked(&addr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QS_ERR_CUDA, std::string("the static sampling array could not be placed on the "
+                                           "device: ") + cudaGetErrorString(e));
+    }
   }
-  uint8_t *base = static_cast<uint8_t *>(g_noalloc_addr[dev]);
+  uint8_t *base = static_cast<uint8_t *>(addr);
   uint64_t *FX = reinterpret_cast<uint64_t *>(base);
   uint64_t *FZ = reinterpret_cast<uint64_t *>(base + fbytes);
   uint64_t *dout = reinterpret_cast<uint64_t *>(base + 2 * fbytes);

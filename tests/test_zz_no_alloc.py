@@ -64,3 +64,43 @@ def test_noalloc_rejects_oversize_request():
         qs.qs_sim_sample_noalloc(sim.sim, shots, 5, out.data_ptr(), M * ow)
     assert e.value.code == -5 and "static scratch" in str(e.value)
     sim.sync()  # nothing was enqueued; the sim is still usable
+
+
+def test_noalloc_with_noise_channels_matches_sample():
+    """The op log's noise channels (the replay_noise branch) go through the
+    static array exactly as through a workspace."""
+    circ = C.with_circuit_noise(C.gate_mix_circuit(120, 14, seed=5, measure_every=4,
+                                                   measure_frac=0.3), 0.02, 0.05)
+    sim = qs.Simulator(circ.n, device="cuda:0")
+    sim.run(circ, seed=9)
+    for shots, seed in [(700, 3), (64, 4)]:
+        want = sim.sample(shots, seed=seed, on_device=False)
+        assert np.array_equal(_noalloc(sim, shots, seed, True), want)
+    sim.sync()
+
+
+def test_noalloc_just_under_the_limit_and_allocates_nothing():
+    """A request whose frames and record need just under QS_NOALLOC_SCRATCH_BYTES
+    (n = 2000, 4 measurements, 66,816 shots: 2 * 2000 * 1044 * 8 + 4 * 1044 * 8
+    = 33,441,408 of 33,554,432 bytes) succeeds and matches qs_sim_sample, and
+    two calls in a row leave the device's free memory unchanged."""
+    n, shots = 2000, 66_816
+    circ = C.random_circuit(n, 6, 0.5, seed=3, final_measure_all=False)
+    sim = qs.Simulator(n, device="cuda:0")
+    sim.run(circ, seed=1)
+    sim.measure(np.array([0, 1, 2, 3], np.uint32), seed=2)
+    ow = (shots + 63) // 64
+    fw = (ow + 3) // 4 * 4
+    assert 2 * n * fw * 8 + 4 * ow * 8 <= (32 << 20) < 2 * n * (fw + 4) * 8 + 4 * (ow + 1) * 8
+    want = sim.sample(shots, seed=11, on_device=True)
+    out = torch.zeros((4, ow), dtype=torch.int64, device="cuda:0")
+    qs.qs_sim_sample_noalloc(sim.sim, shots, 11, out.data_ptr(), 4 * ow)
+    torch.cuda.synchronize()
+    assert torch.equal(out, want)
+    free1 = torch.cuda.mem_get_info()[0]
+    qs.qs_sim_sample_noalloc(sim.sim, shots, 12, out.data_ptr(), 4 * ow)
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert free1 == free2, (free1, free2)
+    assert torch.equal(out, sim.sample(shots, seed=12, on_device=True))
+    sim.sync()
