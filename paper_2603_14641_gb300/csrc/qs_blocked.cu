@@ -51,13 +51,15 @@ struct BlkState {
   int32_t Cp[64];      // parity of (z_V ^ z_orig) . x_orig
   int32_t rV[64];      // sign bit of V_j
   uint64_t G[64];      // G[s] bit t = parity(z_{V_s} . x_{V_t})
-  uint64_t cpiv[64];   // C of the pivot row at its step (one-CTA symbolic pass)
+  uint64_t cpiv[64];   // C of the pivot row at its step (lazy symbolic pass)
   uint32_t err;
+  uint32_t pad2;
+  uint64_t win_or[1024];  // OR of C over each window of 1024 stabilizer rows (lazy pass)
 };
 
 __device__ __forceinline__ int m4(int v) { return ((v % 4) + 4) % 4; }
 
-__global__ void blk_reset_kernel(BlkState *st, int B) {
+__global__ void blk_reset_kernel(BlkState *st, int B, uint32_t nwin) {
   const int t = threadIdx.x;
   if (t < 3) st->slot[t] = kBlkNone;
   if (t == 0) { st->len = B; st->err = 0; }
@@ -65,6 +67,7 @@ __global__ void blk_reset_kernel(BlkState *st, int B) {
     st->piv[t] = kBlkNone; st->mpiv[t] = 0; st->A[t] = 0; st->B0[t] = 0; st->Cp[t] = 0;
     st->rV[t] = 0; st->G[t] = 0;
   }
+  for (uint32_t w = t; w < nwin; w += blockDim.x) st->win_or[w] = 0;
 }
 
 // C_r = x bits of row r at q_0..q_{B-1}; M = 0; base = original; T = parity = 0;
@@ -88,6 +91,14 @@ blk_init_kernel(const uint64_t *__restrict__ RX, uint32_t rs, uint64_t nrows, ui
     C[r] = c;
     M[r] = 0;
     base[r] = kBaseOrig;
+  }
+  {
+    // OR of C over this warp's 32 rows (one window of 1024 stabilizer rows: the
+    // stabilizer half starts at 64 k, a multiple of 32)
+    uint64_t o = (r >= 64ull * k && r < 64ull * k + n) ? c : 0;
+    for (int d = 16; d > 0; d >>= 1) o |= __shfl_xor_sync(0xffffffffu, o, d);
+    if ((threadIdx.x & 31) == 0 && o)
+      atomicOr(reinterpret_cast<unsigned long long *>(&st->win_or[(r - 64ull * k) >> 10]), o);
   }
   const uint32_t ball = __ballot_sync(0xffffffffu, (c & 1ull) != 0);
   if ((threadIdx.x & 31) == 0 && r < nrows) {
@@ -151,58 +162,113 @@ blk_step_kernel(uint64_t nrows, uint32_t n, uint32_t k, int j, int B, const uint
   }
 }
 
-// Symbolic pass in one CTA when the C words of the n stabilizer rows fit in
-// shared memory (n <= kSymSmallRows): after blk_init_kernel, the same result
-// as B blk_step_kernel launches. Only stabilizer rows can be pivots, so the
-// step loop tracks only their C words: each step finds the pivot with a
-// block-wide min and XORs the pivot's C into the stabilizer targets. Every
-// row's M_r and base_r then follow from replaying the recorded pivots
-// (p_j, C_{p_j}) on its original C (blk_replay_kernel, one thread per row).
-constexpr uint32_t kSymSmallRows = 25600;  // 200 KB of C words
-constexpr int kSymThreads = 1024;
+// Lazy symbolic pass in one CTA, for any n: only the pivot sequence
+// (p_j, C_{p_j}) is needed here (blk_replay_kernel then derives every row's M_r
+// and base_r from it), and the pivot of step j is the first stabilizer row, in
+// index order, whose current C has bit j. So the stabilizer rows are scanned in
+// windows of 1024 (one row per thread), in order, and a window's rows are
+// brought up to step j (replaying steps a_w..j-1 on them: the pivot row of a
+// step becomes 0, a row with bit s set takes ^= C_{p_s}) only when it can hold
+// bit j. That is decided from U_w, an upper bound on the OR of the window's C:
+// exact when the window was last replayed, then grown by C_{p_s} for every
+// step s whose bit U_w has (a row that takes C_{p_s} had bit s). In a dense
+// state the pivots come from the first nonzero window, so a step costs one
+// window and one barrier; rows far from the front are never read. Rows of
+// replayed windows live in a working copy (W, the second C buffer); C0 stays
+// intact for the replay kernel.
+constexpr int kLazyThreads = 1024;
+constexpr uint32_t kLazyMaxWindows = 1024;  // n <= 2^20
 
-__global__ void __launch_bounds__(kSymThreads)
-blk_symbolic_small_kernel(uint32_t n, uint32_t k, int B, const uint64_t *__restrict__ C0,
-                          BlkState *st) {
-  extern __shared__ uint64_t sc[];  // [n]: C of stabilizer row 64 k + i
-  __shared__ uint32_t swarp[kSymThreads / 32];
-  __shared__ uint32_t sbest;
-  __shared__ uint64_t scp;
+__device__ __forceinline__ uint64_t lazy_bound(uint64_t u, int a, int j, const uint64_t *cp) {
+  for (int s = a; s < j; ++s)
+    if ((u >> s) & 1ull) u |= cp[s];
+  return u;
+}
+
+__global__ void __launch_bounds__(kLazyThreads)
+blk_lazy_symbolic_kernel(uint32_t n, uint32_t k, int B, const uint64_t *__restrict__ C0,
+                         uint64_t *__restrict__ W, BlkState *st) {
+  __shared__ uint64_t su[kLazyMaxWindows];   // U_w
+  __shared__ uint8_t sa[kLazyMaxWindows];    // a_w: steps replayed on the window's rows
+  __shared__ uint8_t sinit[kLazyMaxWindows]; // rows already in the working copy
+  __shared__ int32_t spiv[64];               // stabilizer index of each step's pivot
+  __shared__ uint64_t scp[64];               // its C at that step
+  __shared__ uint32_t srow[2][32];           // per warp: first row with bit j (or ~0u)
+  __shared__ uint64_t sval[2][32], sor[2][32];
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t nwin = (n + 1023) / 1024;
   const uint64_t lo = 64ull * k;
-  for (uint32_t i = tid; i < n; i += kSymThreads) sc[i] = C0[lo + i];
+  for (uint32_t w = tid; w < nwin; w += kLazyThreads) {
+    su[w] = st->win_or[w];
+    sa[w] = 0;
+    sinit[w] = 0;
+  }
   __syncthreads();
-  int len = B;
+  uint32_t front = 0;  // first window that may hold a nonzero row (uniform)
+  while (front < nwin && su[front] == 0) ++front;
+  int len = B, par = 0;
+  uint32_t cw = 0xFFFFFFFFu;  // window whose row this thread holds in cc
+  uint64_t cc = 0;
   for (int j = 0; j < B; ++j) {
-    // pivot: smallest stabilizer row with bit j set (a thread's rows ascend)
-    uint32_t best = 0xFFFFFFFFu;
-    for (uint32_t i = tid; i < n; i += kSymThreads)
-      if ((sc[i] >> j) & 1ull) { best = i; break; }
-    best = __reduce_min_sync(0xffffffffu, best);
-    if (lane == 0) swarp[warp] = best;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t v = lane < kSymThreads / 32 ? swarp[lane] : 0xFFFFFFFFu;
-      v = __reduce_min_sync(0xffffffffu, v);
-      if (lane == 0) {
-        sbest = v;
-        if (v != 0xFFFFFFFFu) {
-          scp = sc[v];
-          st->piv[j] = (int64_t)(lo + v);
-          st->cpiv[j] = sc[v];
+    uint32_t hit = 0xFFFFFFFFu;
+    uint64_t hitc = 0;
+    for (uint32_t w = front; w < nwin; ++w) {
+      const int a = sa[w];
+      if (!((lazy_bound(su[w], a, j, scp) >> j) & 1ull)) continue;  // no row can have bit j
+      // bring row 1024 w + tid up to step j
+      const uint32_t i = w * 1024 + tid;
+      uint64_t c = 0;
+      if (i < n) {
+        if (cw == w) c = cc;
+        else c = sinit[w] ? W[lo + i] : C0[lo + i];
+        for (int s2 = a; s2 < j; ++s2) {
+          if ((int32_t)i == spiv[s2]) c = 0;
+          else if ((c >> s2) & 1ull) c ^= scp[s2];
         }
+        if (cw != w && cw != 0xFFFFFFFFu) W[lo + cw * 1024 + tid] = cc;  // evict the held row
+        cw = w;
+        cc = c;
+      }
+      const bool has = i < n && ((c >> j) & 1ull);
+      const uint32_t ball = __ballot_sync(0xffffffffu, has);
+      const uint32_t first = ball ? (uint32_t)(__ffs(ball) - 1) : 32u;
+      const uint64_t fc = __shfl_sync(0xffffffffu, c, first & 31);
+      uint64_t o = c;
+      for (int d = 16; d > 0; d >>= 1) o |= __shfl_xor_sync(0xffffffffu, o, d);
+      if (lane == 0) {
+        srow[par][warp] = ball ? warp * 32 + first : 0xFFFFFFFFu;
+        sval[par][warp] = fc;
+        sor[par][warp] = o;
+      }
+      __syncthreads();
+      // every warp reduces the 32 per-warp slots lane-parallel (lane v reads slot v)
+      const uint32_t rv = srow[par][lane];
+      const uint64_t vv = sval[par][lane], ov = sor[par][lane];
+      const uint32_t best = __reduce_min_sync(0xffffffffu, rv);
+      const uint32_t bl = __ffs(__ballot_sync(0xffffffffu, rv == best)) - 1;
+      const uint64_t bc = __shfl_sync(0xffffffffu, vv, bl);
+      const uint64_t wor = ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(ov >> 32)) << 32) |
+                           __reduce_or_sync(0xffffffffu, (uint32_t)ov);
+      par ^= 1;
+      if (tid == 0) {
+        su[w] = wor;
+        sa[w] = (uint8_t)j;
+        sinit[w] = 1;
+      }
+      if (best != 0xFFFFFFFFu) {
+        hit = w * 1024 + best;
+        hitc = bc;
+        break;
       }
     }
-    __syncthreads();
-    const uint32_t b = sbest;
-    if (b == 0xFFFFFFFFu) { len = j; break; }  // deterministic: the block ends before step j
-    const uint64_t cp = scp;
-    for (uint32_t i = tid; i < n; i += kSymThreads) {
-      const uint64_t c = sc[i];
-      if (i == b) sc[i] = 0;
-      else if ((c >> j) & 1ull) sc[i] = c ^ cp;
+    if (hit == 0xFFFFFFFFu) { len = j; break; }  // deterministic: the block ends before step j
+    if (tid == 0) {
+      spiv[j] = (int32_t)hit;
+      scp[j] = hitc;
+      st->piv[j] = (int64_t)(lo + hit);
+      st->cpiv[j] = hitc;
     }
-    __syncthreads();
+    __syncthreads();  // su/sa/sinit and the new pivot are visible to every thread
   }
   if (tid == 0) st->len = len;
 }
@@ -210,24 +276,31 @@ blk_symbolic_small_kernel(uint32_t n, uint32_t k, int B, const uint64_t *__restr
 __global__ void __launch_bounds__(256)
 blk_replay_kernel(uint64_t nrows, uint32_t k, const uint64_t *__restrict__ C0,
                   uint64_t *__restrict__ M, int32_t *__restrict__ base, BlkState *st) {
+  __shared__ int64_t sp[64];
+  __shared__ uint64_t sc[64];
+  const int L = st->len;
+  if (threadIdx.x < 64 && (int)threadIdx.x < L) {
+    sp[threadIdx.x] = st->piv[threadIdx.x];
+    sc[threadIdx.x] = st->cpiv[threadIdx.x];
+  }
+  __syncthreads();
   const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrows) return;
-  const int L = st->len;
   const int64_t lo = 64ll * k;
   uint64_t c = C0[r], m = 0;
   int32_t b = kBaseOrig;
   for (int j = 0; j < L; ++j) {
-    const int64_t p = st->piv[j];
+    const int64_t p = sp[j];
     if ((int64_t)r == p) {
       st->mpiv[j] = m;
       b = kBasePivot + j;
       c = 0;
     } else if ((int64_t)r == p - lo) {
-      c = st->cpiv[j];
+      c = sc[j];
       m = 0;
       b = j;
     } else if ((c >> j) & 1ull) {
-      c ^= st->cpiv[j];
+      c ^= sc[j];
       m |= 1ull << j;
     }
   }
@@ -671,20 +744,17 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(blk_vrows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kVrowSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(blk_symbolic_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(kSymSmallRows * sizeof(uint64_t)));
     return e;
   });
   if (ea != cudaSuccess) return ea;
   tbegin(d.timer, QS_TIME_BLK_SYMBOLIC, s);
-  blk_reset_kernel<<<1, 64, 0, s>>>(st, B);
+  const uint32_t nwin = (L.n + 1023) / 1024;
+  blk_reset_kernel<<<1, 256, 0, s>>>(st, B, nwin);
   blk_init_kernel<<<rb, 256, 0, s>>>(d.RX, L.rs, L.nrows, L.n, L.k, qubits, B, C0, M, base, st,
                                      d.err);
   int sym_launches = B;
-  if (L.n <= kSymSmallRows && !d.step_symbolic) {
-    blk_symbolic_small_kernel<<<1, kSymThreads, (size_t)L.n * sizeof(uint64_t), s>>>(L.n, L.k, B, C0,
-                                                                                     st);
+  if (!d.step_symbolic) {
+    blk_lazy_symbolic_kernel<<<1, kLazyThreads, 0, s>>>(L.n, L.k, B, C0, C1, st);
     blk_replay_kernel<<<rb, 256, 0, s>>>(L.nrows, L.k, C0, M, base, st);
     sym_launches = 2;
   } else {

@@ -21,8 +21,11 @@
 namespace qs {
 
 // grid.x = ceil(nwords / WPB); block owns words [WPB * blockIdx.x, +WPB) of every column.
-// lptr: L + 1 gate offsets (absolute indices into packed).
-template <bool SIGNS, int WPB>
+// lptr: L + 1 gate offsets (absolute indices into packed). R >= the gates of
+// any layer / blockDim.x: a thread issues the loads of all its gate records of
+// a layer (and the next layer's end offset) before it applies any of them, so
+// each layer costs one memory latency rather than one per gate.
+template <bool SIGNS, int WPB, int R>
 __global__ void __launch_bounds__(1024)
 fused_segment_kernel(uint64_t *__restrict__ X, uint64_t *__restrict__ Z, uint64_t *__restrict__ S,
                      uint32_t n, uint32_t stride, uint32_t nwords,
@@ -44,10 +47,20 @@ fused_segment_kernel(uint64_t *__restrict__ X, uint64_t *__restrict__ Z, uint64_
 #pragma unroll
   for (int j = 0; j < WPB; ++j) sacc[j] = 0;
   bool bad = false;
+  const uint2 *rec2 = reinterpret_cast<const uint2 *>(packed);
+  int64_t ga = L ? lptr[0] : 0, gb = L ? lptr[1] : 0;
   for (uint32_t l = 0; l < L; ++l) {
-    const int64_t g1 = lptr[l + 1];
-    for (int64_t g = lptr[l] + threadIdx.x; g < g1; g += blockDim.x) {
-      const uint32_t w = __ldg(packed + 2 * g), qb = __ldg(packed + 2 * g + 1);
+    const int64_t gn = (l + 2 <= L) ? __ldg(lptr + l + 2) : gb;  // next layer's end
+    uint2 rec[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int64_t g = ga + threadIdx.x + (int64_t)i * blockDim.x;
+      rec[i] = g < gb ? __ldg(rec2 + g) : make_uint2(0, 0);
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      if (ga + threadIdx.x + (int64_t)i * blockDim.x >= gb) break;
+      const uint32_t w = rec[i].x, qb = rec[i].y;
       const uint32_t type = w >> 24, qa = w & 0xFFFFFFu;
       const bool two = type >= QS_CX && type <= QS_ISWAP;
       if (qa >= n || type >= QS_NUM_GATE_TYPES || (two && (qb >= n || qb == qa))) {
@@ -65,6 +78,8 @@ fused_segment_kernel(uint64_t *__restrict__ X, uint64_t *__restrict__ Z, uint64_
       }
     }
     __syncthreads();
+    ga = gb;
+    gb = gn;
   }
   if (bad && blockIdx.x == 0) atomicOr(err, kErrBadGate);
   for (uint32_t q = threadIdx.x; q < n; q += blockDim.x) {
@@ -94,6 +109,7 @@ fused_segment_kernel(uint64_t *__restrict__ X, uint64_t *__restrict__ Z, uint64_
 }
 
 constexpr size_t kFusedSmemMax = 220 * 1024;
+constexpr uint32_t kFusedThreads = 1024;
 
 int fused_words_per_block(uint32_t n, uint32_t nwords) {
   // widest slice that fits shared memory while keeping at least one block per SM
@@ -105,38 +121,53 @@ int fused_words_per_block(uint32_t n, uint32_t nwords) {
 
 bool fused_fits(uint32_t n) { return (size_t)16 * n <= kFusedSmemMax; }
 
-template <bool SIGNS, int WPB>
+template <bool SIGNS, int WPB, int R>
 static cudaError_t launch_fused_t(uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t n, uint32_t stride,
                                   uint32_t nwords, const uint32_t *packed, const int64_t *lptr,
                                   uint32_t L, uint32_t *err, cudaStream_t s) {
   static std::atomic<uint64_t> attr_set{0};  // one bit per device ordinal
   cudaError_t ea = once_per_device(attr_set, []() {
-    return cudaFuncSetAttribute(fused_segment_kernel<SIGNS, WPB>,
+    return cudaFuncSetAttribute(fused_segment_kernel<SIGNS, WPB, R>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemMax);
   });
   if (ea != cudaSuccess) return ea;
   const size_t smem = (size_t)16 * n * WPB;
   const uint32_t blocks = (nwords + WPB - 1) / WPB;
-  uint32_t threads = 1024;
-  fused_segment_kernel<SIGNS, WPB><<<blocks, threads, smem, s>>>(X, Z, S, n, stride, nwords, packed,
-                                                                 lptr, L, err);
+  fused_segment_kernel<SIGNS, WPB, R><<<blocks, kFusedThreads, smem, s>>>(X, Z, S, n, stride, nwords,
+                                                                          packed, lptr, L, err);
   return cudaGetLastError();
+}
+
+template <bool SIGNS, int WPB>
+static cudaError_t launch_fused_r(uint32_t max_gates, uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t n,
+                                  uint32_t stride, uint32_t nwords, const uint32_t *packed,
+                                  const int64_t *lptr, uint32_t L, uint32_t *err, cudaStream_t s) {
+  // a layer holds at most n gates and a WPB-word slice of 16 n WPB bytes fits
+  // 220 KB, so R <= 16 for one word, 8 for two and 4 for four
+  const uint32_t r = (max_gates + kFusedThreads - 1) / kFusedThreads;
+  if (r <= 1) return launch_fused_t<SIGNS, WPB, 1>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s);
+  if (r <= 2) return launch_fused_t<SIGNS, WPB, 2>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s);
+  if (r <= 4) return launch_fused_t<SIGNS, WPB, 4>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s);
+  if constexpr (WPB <= 2)
+    if (r <= 8) return launch_fused_t<SIGNS, WPB, 8>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s);
+  if constexpr (WPB == 1)
+    if (r <= 16) return launch_fused_t<SIGNS, WPB, 16>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fused_segment(uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t n, uint32_t stride,
                                  uint32_t nwords, const uint32_t *packed, const int64_t *lptr,
-                                 uint32_t L, uint32_t *err, cudaStream_t s) {
+                                 uint32_t L, uint32_t max_gates, uint32_t *err, cudaStream_t s) {
   const int wpb = fused_words_per_block(n, nwords);
   const bool signs = S != nullptr;
-  if (wpb == 4)
-    return signs ? launch_fused_t<true, 4>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s)
-                 : launch_fused_t<false, 4>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s);
-  if (wpb == 2)
-    return signs ? launch_fused_t<true, 2>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s)
-                 : launch_fused_t<false, 2>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s);
-  if (wpb == 1)
-    return signs ? launch_fused_t<true, 1>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s)
-                 : launch_fused_t<false, 1>(X, Z, S, n, stride, nwords, packed, lptr, L, err, s);
+#define QS_FUSED_CASE(W)                                                                          \
+  if (wpb == W)                                                                                   \
+    return signs ? launch_fused_r<true, W>(max_gates, X, Z, S, n, stride, nwords, packed, lptr, L, err, s) \
+                 : launch_fused_r<false, W>(max_gates, X, Z, S, n, stride, nwords, packed, lptr, L, err, s);
+  QS_FUSED_CASE(4)
+  QS_FUSED_CASE(2)
+  QS_FUSED_CASE(1)
+#undef QS_FUSED_CASE
   return cudaErrorInvalidValue;
 }
 

@@ -238,8 +238,9 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
 // fused segment of L layers on a word-sliced, shared-memory-resident tableau
 // (S == nullptr: frames, no signs); lptr: L + 1 device gate offsets
 bool fused_fits(uint32_t n);
+// max_gates: the largest layer of the segment (gates)
 cudaError_t launch_fused_segment(uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t n, uint32_t stride,
                                  uint32_t nwords, const uint32_t *packed, const int64_t *lptr,
-                                 uint32_t L, uint32_t *err, cudaStream_t s);
+                                 uint32_t L, uint32_t max_gates, uint32_t *err, cudaStream_t s);
 
 }  // namespace qs

@@ -244,9 +244,11 @@ int run_dev_layers(qs_sim *s, uint64_t *X, uint64_t *Z, uint64_t *S, uint32_t st
       memcpy(h, ptr + l0, (L + 1) * 8);
       int rc = upload(s, slot, (L + 1) * 8);
       if (rc) return rc;
+      int64_t max_gates = 0;  // layers hold at most n gates (checked when they were added)
+      for (size_t l = l0; l < l0 + L; ++l) max_gates = std::max<int64_t>(max_gates, ptr[l + 1] - ptr[l]);
       QS_CUDA(s, launch_fused_segment(X, Z, S, n, stride, stride, packed,
                                       reinterpret_cast<const int64_t *>(s->dstage), (uint32_t)L,
-                                      s->d.err, s->stream));
+                                      (uint32_t)max_gates, s->d.err, s->stream));
       s->launches += 1;
     }
     return QS_OK;
