@@ -402,12 +402,70 @@ def run_ours(args):
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, circ)
+    sim.close()
+    del packed_dev, qdev, rec_dev, fws
+    torch.cuda.empty_cache()
+    if rank == 0 and ws == 1 and args.workload == "n180k" and not args.no_extras:
+        # the other configurations, compact, so that every bench run records them
+        out["serve"] = serve_measure(args, args.serve_count, sweep=False, cpu=False)
+        out["batch"] = batch_measure(args, steps=2, warmup=1, cpu=False)
+        out["inverse_tableau_10k"] = inverse_mode_summary()
     if rank == 0:
         print(json.dumps(out))
-    sim.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def inverse_mode_summary():
+    """F1 on the 10,000-qubit workload: the whole program (1,000 layers, 19,500
+    measurements) in the inverse-tableau mode (Alg. 1's elimination, one
+    measurement at a time) and in the default CHP mode (blocked), timed once
+    each with CUDA events after a warm-up run; records must be identical."""
+    import torch
+    from paper_2603_14641_gb300 import qs
+    circ = C.workload_10k()
+    res = {}
+    recs = {}
+    for name, flags in (("inverse", qs.QS_FLAG_INVERSE_TABLEAU), ("chp", 0)):
+        stream = torch.cuda.Stream()
+        sim = qs.Simulator(circ.n, device="cuda:0", stream=stream, flags=flags)
+        dc = sim.upload(circ)
+        qd = [torch.from_numpy(np.asarray(op[1], np.uint32).view(np.int32)).cuda()
+              if op[0] == "measure" else None for op in circ.ops]
+        ev = {k: [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True), 0.0]
+              for k in ("layers", "measure")}
+
+        def run(timed):
+            qs.qs_sim_reset(sim.sim, None)
+            for op, q in zip(circ.ops, qd):
+                e = ev["layers" if op[0] == "layers" else "measure"]
+                if timed:
+                    e[0].record(stream)
+                if op[0] == "layers":
+                    qs.qs_sim_apply_layers_dev(sim.sim, dc.packed.data_ptr(), dc.layer_ptr, op[1], op[2])
+                else:
+                    qs.qs_sim_measure_dev(sim.sim, q.data_ptr(), q.numel(), 77, 0)
+                if timed:
+                    e[1].record(stream)
+                    e[1].synchronize()
+                    e[2] += e[0].elapsed_time(e[1])
+
+        run(False)
+        torch.cuda.synchronize()
+        run(True)
+        recs[name] = sim.record()
+        sim.sync()
+        g_ms, m_ms = ev["layers"][2], ev["measure"][2]
+        res[name] = {"gates_ms": g_ms, "measure_ms": m_ms, "total_ms": g_ms + m_ms,
+                     "gates_per_s": circ.n_gates / (g_ms / 1e3),
+                     "measurements_per_s": circ.n_measurements / (m_ms / 1e3)}
+        sim.close()
+    res["records_identical"] = bool(np.array_equal(recs["inverse"], recs["chp"]))
+    res["what"] = ("10,000 qubits, 1,000 layers, 19,500 measurements (19 windows of 500 and a final "
+                   "round of 10,000); inverse mode: one layer kernel per layer and four launches per "
+                   "measurement (Alg. 1); chp: fused gate segments and blocked measurement")
+    return res
 
 
 def apply_roofline(ktimes, n, hbm, peak_kind):
@@ -637,12 +695,13 @@ def cpu_baseline(args, circ):
             "host_cores_available": os.cpu_count()}
 
 
-def run_batch(args):
+def batch_measure(args, steps: int, warmup: int, subset_every: int = 8, cpu: bool = True):
     """Batched workload: 512 independent circuits (n log-uniform 50..5,000,
-    depth 200, 10% of qubits measured after every 10th layer) in one
-    persistent launch, against the same circuits run one at a time through the
-    single-circuit path on the same GPU (a seeded subset of every 8th circuit
-    for the one-at-a-time leg, whose launches take tens of seconds for all 512)."""
+    depth 200, 10% of qubits measured after every 10th layer) through qs_batch
+    (the n < 1024 circuits in one persistent launch), against the same
+    circuits run one at a time through the single-circuit path on the same GPU
+    (a seeded subset of every `subset_every`-th circuit for the one-at-a-time
+    leg, whose launches take tens of seconds for all 512)."""
     import torch
     from paper_2603_14641_gb300 import qs
     torch.cuda.set_device(0)
@@ -670,13 +729,13 @@ def run_batch(args):
         torch.cuda.synchronize()
         return a.elapsed_time(e) / steps
 
-    ms_batch = timed(lambda: b.run(tuning), args.steps, args.warmup)
+    ms_batch = timed(lambda: b.run(tuning), steps, warmup)
     b.sync()
     # one circuit at a time through the single-circuit path (subset)
-    idx = list(range(0, len(circs), 8))
+    idx = list(range(0, len(circs), subset_every))
     sub = [circs[i] for i in idx]
     bs = qs.Batch(sub, [seeds[i] for i in idx], device=str(dev), stream=stream)
-    ms_batch_sub = timed(lambda: bs.run(tuning), args.steps, args.warmup)
+    ms_batch_sub = timed(lambda: bs.run(tuning), steps, warmup)
     bs.sync()
     sims, dcs, qd = [], [], []
     for c in sub:
@@ -699,25 +758,33 @@ def run_batch(args):
     identical = all(np.array_equal(s_.record(), b.record(i)) for s_, i in zip(sims, idx))
     g_sub = sum(c.n_gates for c in sub)
     m_sub = sum(c.n_measurements for c in sub)
-    cpu = None
-    if not args.no_cpu_baseline:
-        cpu = batch_cpu_baseline(circs, seeds)
-    out = {"metric": "batched Clifford circuits: gates/s and measurements/s, one persistent "
-                     "launch vs one circuit at a time",
-           "value": gates / (ms_batch / 1e3), "unit": "gates/s", "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-           "data": "synthetic",
+    out = {"value": gates / (ms_batch / 1e3), "unit": "gates/s", "ms_per_run": ms_batch,
+           "measurements_per_s": meas / (ms_batch / 1e3),
            "config": {"workload": f"{len(circs)} random Clifford circuits, n log-uniform "
                                   "50..5000, depth 200, p_cx 0.5, 10% measured every 10 layers",
                       "gates": gates, "measurements": meas,
                       "tuning": tuning.as_dict(), "autotune_s": tune_s},
-           "measurements_per_s": meas / (ms_batch / 1e3),
            "subset": {"circuits": len(sub), "gates": g_sub, "measurements": m_sub,
                       "batch_ms": ms_batch_sub, "one_at_a_time_ms": ms_single_sub,
                       "speedup": ms_single_sub / ms_batch_sub,
-                      "records_identical": bool(identical)},
-           "cpu_baseline": cpu}
+                      "records_identical": bool(identical)}}
+    if cpu:
+        out["cpu_baseline"] = batch_cpu_baseline(circs, seeds)
+    for s_ in sims:
+        s_.close()
+    return out
+
+
+def run_batch(args):
+    r = batch_measure(args, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
+    out = {"metric": "batched Clifford circuits: gates/s and measurements/s, one persistent "
+                     "launch vs one circuit at a time",
+           "value": r["value"], "unit": "gates/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_run"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+           "data": "synthetic", "config": r["config"],
+           "measurements_per_s": r["measurements_per_s"], "subset": r["subset"],
+           "cpu_baseline": r.get("cpu_baseline")}
     print(json.dumps(out))
 
 
@@ -744,16 +811,16 @@ def batch_cpu_baseline(circs, seeds, budget_s: float = 15.0):
                       f"(every 16th), smallest first, {dt:.1f} s of CPU"}
 
 
-def run_serve(args):
+def serve_measure(args, count: int, sweep: bool = True, cpu: bool = True):
     """Serving workload: Poisson stream of requests (n log-uniform 100..20,000,
     depth 100..500, shots log-uniform 1e3..1e6, each ending with a Z-measurement
     of every qubit). Measures the saturation rate (all requests at t = 0), then
-    p50/p99 latency and shots/s at 0.5x, 1x and 2x that rate, and the same
-    requests served one at a time (one slot) on the same GPU."""
+    (if `sweep`) p50/p99 latency and shots/s at 0.5x, 1x and 2x that rate, and the
+    same requests served one at a time (one slot) on the same GPU."""
     import torch
     from paper_2603_14641_gb300 import serve
     torch.cuda.set_device(0)
-    specs = C.serving_requests(args.serve_count, rate_hz=1.0, seed=5)
+    specs = C.serving_requests(count, rate_hz=1.0, seed=5)
     circs = [C.random_circuit(r.n, r.depth, 0.5, seed=r.seed) for r in specs]
     unit_t = np.array([r.arrival_s for r in specs])
 
@@ -762,38 +829,68 @@ def run_serve(args):
                 for i in range(len(specs))]
 
     budget = args.serve_budget_gb << 30
-    # warm-up: a few small requests through every slot
+
+    def fingerprint(res):
+        # records in full, samples as (shape, XOR and wrapping sum of the words); the
+        # results (samples in pinned host memory) are released before the next run,
+        # as a server hands them off, so the pinned-memory cache is reused
+        out = {}
+        for r in res:
+            s = r.samples
+            out[r.rid] = (r.record.tobytes(), None if s is None else
+                          (s.shape, int(np.bitwise_xor.reduce(s, axis=None)) if s.size else 0,
+                           int(np.add.reduce(s, axis=None, dtype=np.uint64)) if s.size else 0))
+        return out
+
+    # warm-up: a few small requests through every slot, then the whole stream once
     serve.serve(reqs(0.0)[:args.serve_slots], slots=args.serve_slots, budget_bytes=budget,
-                device="cuda:0", keep_samples=False)
-    sat_res, sat, _ = serve.serve(reqs(0.0), slots=args.serve_slots, budget_bytes=budget,
-                                  device="cuda:0", keep_samples=False)
+                device="cuda:0")
+    serve.serve(reqs(0.0), slots=args.serve_slots, budget_bytes=budget, device="cuda:0")
+    sat_res, sat, sat_st = serve.serve(reqs(0.0), slots=args.serve_slots, budget_bytes=budget,
+                                       device="cuda:0")
+    sat_fp = fingerprint(sat_res)
+    del sat_res
     sat_rate = len(specs) / sat["makespan_s"]
-    sweep = {}
-    for mult in (0.5, 1.0, 2.0):
-        rate = mult * sat_rate
-        res, summ, st = serve.serve(reqs(1.0 / rate), slots=args.serve_slots, budget_bytes=budget,
-                                    device="cuda:0", keep_samples=False)
-        summ.update({"rate_hz": rate, "peak_active": st["peak_active"],
-                     "peak_bytes": st["peak_bytes"]})
-        sweep[f"{mult}x"] = summ
+    sweep_out = {}
+    if sweep:
+        for mult in (0.5, 1.0, 2.0):
+            rate = mult * sat_rate
+            res, summ, st = serve.serve(reqs(1.0 / rate), slots=args.serve_slots,
+                                        budget_bytes=budget, device="cuda:0")
+            summ.update({"rate_hz": rate, "peak_active": st["peak_active"],
+                         "peak_bytes": st["peak_bytes"], "batches": st["batches"],
+                         "batched_requests": st["batched_requests"]})
+            sweep_out[f"{mult}x"] = summ
+            del res
+    # one request at a time: one slot and no batching
     one_res, one, _ = serve.serve(reqs(0.0), slots=1, budget_bytes=budget, device="cuda:0",
-                                  keep_samples=False)
-    same = all(np.array_equal(a.record, b.record) for a, b in zip(sat_res, one_res))
+                                  batching=False)
+    same = fingerprint(one_res) == sat_fp
+    del one_res
     shots = sum(r.shots for r in specs)
-    out = {"metric": "served many-shot sampling: p50/p99 latency and shots/s under a Poisson "
-                     "request stream (continuous batching vs one request at a time)",
-           "value": sat["shots_per_s"], "unit": "shots/s", "n_gpus": 1, "higher_is_better": True,
-           "data": "synthetic", "dtype": "u64",
+    out = {"value": sat["shots_per_s"], "unit": "shots/s",
            "config": {"requests": len(specs), "slots": args.serve_slots,
                       "budget_bytes": budget, "shots_total": shots,
                       "n_range": [int(min(c.n for c in circs)), int(max(c.n for c in circs))],
                       "workload": "n log-uniform 100..20000, depth 100..500, shots log-uniform "
-                                  "1e3..1e6, final Z-measurement of all qubits"},
-           "saturation": sat, "saturation_rate_hz": sat_rate, "sweep": sweep,
+                                  "1e3..1e6, final Z-measurement of all qubits; samples returned "
+                                  "to pinned host memory"},
+           "saturation": sat, "saturation_rate_hz": sat_rate,
+           "saturation_batches": {"batches": sat_st["batches"],
+                                  "batched_requests": sat_st["batched_requests"]},
+           "sweep": sweep_out,
            "one_at_a_time": one, "speedup_vs_one_at_a_time": one["makespan_s"] / sat["makespan_s"],
-           "records_identical_alone_and_mixed": bool(same)}
-    if not args.no_cpu_baseline:
+           "results_identical_alone_and_mixed": bool(same)}
+    if cpu:
         out["cpu_baseline"] = serve_cpu_baseline(specs, circs)
+    return out
+
+
+def run_serve(args):
+    r = serve_measure(args, args.serve_count, sweep=True, cpu=not args.no_cpu_baseline)
+    out = {"metric": "served many-shot sampling: p50/p99 latency and shots/s under a Poisson "
+                     "request stream (continuous batching vs one request at a time)",
+           "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "u64", **r}
     print(json.dumps(out))
 
 
@@ -919,6 +1016,8 @@ def main():
                     help="circuit-level Pauli noise of the extra noisy-sampling phase (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the compact serving, batch and inverse-tableau summaries")
     ap.add_argument("--no-full-job", action="store_true",
                     help="skip the once-timed complete 180k program (all final measurements)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

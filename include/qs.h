@@ -470,6 +470,26 @@ int qs_batch_export_rows(qs_batch *batch, uint32_t circuit, const uint32_t *rows
 int qs_batch_autotune(qs_batch *batch, uint32_t round_limit, const char *cache_path,
                       qs_batch_tuning *best);
 
+/*
+ * Pauli-frame sampling (Sec. 5, Alg. 9) of the batch's circuits after a
+ * complete qs_batch_run: circuit c gets shots[c] shots (0 skips it) with frame
+ * seed seeds[c] into records[c], a DEVICE pointer of [M_c][ceil(shots[c]/64)]
+ * words (M_c = the circuit's measurements; bit s of word j = shot 64 j + s,
+ * bits >= shots[c] are 0). The words are those qs_sim_sample gives for the same
+ * circuit alone with that seed: the reference record is the circuit's batch
+ * record and the frame rules are the same. The circuits of n < 1024 are sampled
+ * in ONE launch on the batch's stream (a block per circuit and 64-shot word runs
+ * the circuit's whole program on frames in shared memory); the others replay
+ * their simulators' op logs on the worker streams, which the batch stream then
+ * waits for. The paper has no batch mode; this serves many small sampling
+ * requests at once. Allocates a small table on the batch's stream and waits
+ * for its upload; the sampling itself is only enqueued (qs_batch_sync waits).
+ * Errors: QS_ERR_ARG (NULL arrays, a NULL records[c] with shots[c] > 0,
+ * shots above 2e9), QS_ERR_STATE (no complete run yet, e.g. only a round_limit
+ * run or autotuning since create).
+ */
+int qs_batch_sample(qs_batch *batch, const uint64_t *shots, const uint64_t *seeds, uint64_t *const *records);
+
 /* Message for the last batch error on the calling thread. */
 const char *qs_batch_last_error(void);
 

@@ -527,6 +527,88 @@ __global__ void __launch_bounds__(1024) batch_kernel(BProg P, uint32_t round_lim
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batched Pauli-frame sampling (Sec. 5, Alg. 9) of the persistent part's
+// circuits, one launch for all of them: an item is (circuit, 64-shot word);
+// a block runs the circuit's whole program on that word's frame slice held
+// in shared memory (X~, Z~ of every qubit, 16 n bytes): frame init from the
+// keyed Philox words, every layer's gates without signs (barrier between
+// layers), and for each measurement m of qubit q the output X~[q] ^ ref[m]
+// followed by Z~[q] <- the keyed word of event m + 1. Frames of different
+// shot words never interact, so the items are independent. The words equal
+// qs_sim_sample's for the same circuit and seed.
+// ---------------------------------------------------------------------------
+struct BSampleCirc {
+  uint32_t c, nrounds, rtab, ow;  // circuit, rounds, offset of its round table, shot words
+  uint64_t shots, seed;
+  uint64_t *out;                  // [M][ow] words
+};
+
+__global__ void __launch_bounds__(128)
+batch_sample_kernel(const BCirc *__restrict__ circs, const BSampleCirc *__restrict__ sc, uint32_t nsc,
+                    const uint64_t *__restrict__ pre, const uint32_t *__restrict__ rtab,
+                    uint64_t total, uint32_t *__restrict__ err) {
+  extern __shared__ uint64_t fr[];  // [2][nmax]
+  const uint32_t tid = threadIdx.x;
+  for (uint64_t item = blockIdx.x; item < total; item += gridDim.x) {
+    uint32_t lo = 0, hi = nsc;  // circuit s with pre[s] <= item < pre[s + 1]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (pre[mid] <= item) lo = mid; else hi = mid;
+    }
+    const BSampleCirc S = sc[lo];
+    const BCirc &C = circs[S.c];
+    const uint32_t n = C.n;
+    const uint64_t j = item - pre[lo];
+    uint64_t *FX = fr, *FZ = fr + n;
+    for (uint32_t q = tid; q < n; q += blockDim.x) {
+      FX[q] = 0;
+      FZ[q] = philox4x64_10(0, q, j >> 2, 1, S.seed, kFrameKey).v[j & 3];
+    }
+    __syncthreads();
+    const uint64_t mask = (j == S.ow - 1 && (S.shots & 63)) ? (1ull << (S.shots & 63)) - 1 : ~0ull;
+    const uint32_t *rl = rtab + S.rtab, *rm = rl + S.nrounds + 1;
+    for (uint32_t r = 0; r < S.nrounds; ++r) {
+      for (uint32_t l = rl[r]; l < rl[r + 1]; ++l) {
+        const int64_t g1 = C.lptr[l + 1];
+        for (int64_t g = C.lptr[l] + tid; g < g1; g += blockDim.x) {
+          const uint32_t w = C.gates[2 * g], qb = C.gates[2 * g + 1];
+          const uint32_t type = w >> 24, qa = w & 0xFFFFFFu;
+          const bool two = type >= QS_CX && type <= QS_ISWAP;
+          if (qa >= n || type >= QS_NUM_GATE_TYPES || (two && (qb >= n || qb == qa))) {
+            atomicOr(err, kErrBadGate);
+            continue;
+          }
+          uint64_t xa = FX[qa], za = FZ[qa], xb = 0, zb = 0, s = 0;
+          if (two) { xb = FX[qb]; zb = FZ[qb]; }
+          rule<false>(type, xa, za, xb, zb, s);
+          FX[qa] = xa;
+          FZ[qa] = za;
+          if (two) { FX[qb] = xb; FZ[qb] = zb; }
+        }
+        __syncthreads();
+      }
+      // measurements of the round: outputs read X~ only; Z~[q] takes the word
+      // of the last measurement of q in the round
+      const uint32_t m0 = rm[r], m1 = rm[r + 1];
+      for (uint32_t m = m0 + tid; m < m1; m += blockDim.x) {
+        const uint32_t q = C.qubits[m];
+        const uint64_t ref = C.record[m] ? ~0ull : 0ull;
+        S.out[(uint64_t)m * S.ow + j] = (FX[q] ^ ref) & mask;
+      }
+      __syncthreads();
+      for (uint32_t m = m0 + tid; m < m1; m += blockDim.x) {
+        const uint32_t q = C.qubits[m];
+        bool last = true;
+        for (uint32_t m2 = m + 1; m2 < m1; ++m2)
+          if (C.qubits[m2] == q) { last = false; break; }
+        if (last) FZ[q] = philox4x64_10((uint64_t)m + 1, q, j >> 2, 1, S.seed, kFrameKey).v[j & 3];
+      }
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace qs
 
 using namespace qs;
@@ -587,6 +669,7 @@ struct qs_batch {
   std::vector<cudaEvent_t> wevents;
   cudaEvent_t start_ev = nullptr;       // worker streams start after the batch stream's earlier work
   bool skip_sims = false;               // set while autotuning the persistent kernel
+  bool ran_full = false;                // the records are those of a complete qs_batch_run
 };
 
 static void free_sims(qs_batch *b) {
@@ -1062,6 +1145,7 @@ int qs_batch_run(qs_batch *b, const qs_batch_tuning *tuning, uint32_t round_limi
 static int batch_run(qs_batch *b, const qs_batch_tuning *tuning, uint32_t round_limit) {
   if (!b) return bfail(QS_ERR_ARG, "batch is NULL");
   if (b->broken) return bfail(QS_ERR_STATE, "batch is unusable after an earlier device error");
+  b->ran_full = (round_limit == 0 || round_limit >= b->nrounds) && !b->skip_sims;
   int rc = QS_OK;
   const bool sims = !b->skip_sims && !b->sims.empty();
   if (sims && cudaEventRecord(b->start_ev, b->stream) != cudaSuccess)
@@ -1273,6 +1357,90 @@ int qs_batch_autotune(qs_batch *b, uint32_t round_limit, const char *cache_path,
       << " " << best_t.fuse_depth << "\n";
   }
   return best_ms < 1e29f ? QS_OK : bfail(QS_ERR_INTERNAL, "no tuning candidate ran");
+}
+
+int qs_batch_sample(qs_batch *b, const uint64_t *shots, const uint64_t *seeds, uint64_t *const *records) {
+  if (!b) return bfail(QS_ERR_ARG, "batch is NULL");
+  if (b->broken) return bfail(QS_ERR_STATE, "batch is unusable after an earlier device error");
+  if (!shots || !seeds || !records) return bfail(QS_ERR_ARG, "NULL argument");
+  if (!b->ran_full) return bfail(QS_ERR_STATE, "sampling needs the records of a complete qs_batch_run");
+  // small circuits: one launch; a table of the sampled circuits, their round
+  // tables and the prefix of their shot words
+  std::vector<BSampleCirc> sc;
+  std::vector<uint64_t> pre(1, 0);
+  std::vector<uint32_t> rt;
+  uint32_t nmax = 1;
+  for (uint32_t c = 0; c < b->count; ++c) {
+    if (shots[c] == 0) continue;
+    if (shots[c] > 2000000000ull) return bfail(QS_ERR_ARG, "shots must be at most 2e9");
+    if (!records[c] && b->meas_total[c]) return bfail(QS_ERR_ARG, "records[c] is NULL");
+    if (b->sim_of[c] >= 0 || b->meas_total[c] == 0) continue;  // large, or nothing to record
+    BSampleCirc x{};
+    x.c = c;
+    x.nrounds = (uint32_t)b->rl[c].size() - 1;
+    x.rtab = (uint32_t)rt.size();
+    x.ow = (uint32_t)((shots[c] + 63) / 64);
+    x.shots = shots[c];
+    x.seed = seeds[c];
+    x.out = records[c];
+    rt.insert(rt.end(), b->rl[c].begin(), b->rl[c].end());
+    rt.insert(rt.end(), b->rm[c].begin(), b->rm[c].end());
+    sc.push_back(x);
+    pre.push_back(pre.back() + x.ow);
+    nmax = std::max(nmax, b->circs[c].n);
+  }
+  if (!sc.empty()) {
+    const size_t bytes_sc = sc.size() * sizeof(BSampleCirc), bytes_pre = pre.size() * 8,
+                 bytes_rt = rt.size() * 4;
+    const size_t off_pre = (bytes_sc + 255) & ~size_t(255), off_rt = off_pre + ((bytes_pre + 255) & ~size_t(255));
+    std::vector<uint8_t> host(off_rt + bytes_rt);
+    memcpy(host.data(), sc.data(), bytes_sc);
+    memcpy(host.data() + off_pre, pre.data(), bytes_pre);
+    memcpy(host.data() + off_rt, rt.data(), bytes_rt);
+    void *dev = nullptr;
+    cudaError_t e = cudaMallocAsync(&dev, host.size(), b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) {
+      uint8_t *d = static_cast<uint8_t *>(dev);
+      const uint64_t total = pre.back();
+      const uint32_t grid = (uint32_t)std::min<uint64_t>(total, (uint64_t)b->sms * 16);
+      batch_sample_kernel<<<grid, 128, (size_t)2 * nmax * 8, b->stream>>>(
+          b->d_circs, reinterpret_cast<const BSampleCirc *>(d), (uint32_t)sc.size(),
+          reinterpret_cast<const uint64_t *>(d + off_pre), reinterpret_cast<const uint32_t *>(d + off_rt),
+          total, b->d_err);
+      e = cudaGetLastError();
+      // the host table must outlive the copy: wait for it before returning
+      if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+      if (cudaFreeAsync(dev, b->stream) != cudaSuccess) cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+      b->broken = true;
+      return bfail(QS_ERR_CUDA, std::string("batch sampling: ") + cudaGetErrorString(e));
+    }
+  }
+  // large circuits: their own simulators replay their op logs on the worker streams
+  bool any_large = false;
+  for (uint32_t c = 0; c < b->count; ++c) any_large |= shots[c] > 0 && b->sim_of[c] >= 0;
+  if (any_large) {
+    if (cudaEventRecord(b->start_ev, b->stream) != cudaSuccess)
+      return bfail(QS_ERR_CUDA, "batch event record failed");
+    const uint32_t nw = (uint32_t)b->wstreams.size();
+    for (uint32_t w = 0; w < nw; ++w)
+      if (cudaStreamWaitEvent(b->wstreams[w], b->start_ev, 0) != cudaSuccess)
+        return bfail(QS_ERR_CUDA, "worker stream wait failed");
+    for (uint32_t c = 0; c < b->count; ++c) {
+      if (!(shots[c] > 0 && b->sim_of[c] >= 0)) continue;
+      BSim &x = b->sims[b->sim_of[c]];
+      const uint64_t ow = (shots[c] + 63) / 64;
+      const int rc = qs_sim_sample(x.sim, shots[c], seeds[c], records[c], b->meas_total[c] * ow, nullptr, 0);
+      if (rc) return bfail(rc, std::string("circuit ") + std::to_string(c) + ": " + qs_last_error());
+    }
+    for (uint32_t w = 0; w < nw; ++w)
+      if (cudaEventRecord(b->wevents[w], b->wstreams[w]) != cudaSuccess ||
+          cudaStreamWaitEvent(b->stream, b->wevents[w], 0) != cudaSuccess)
+        return bfail(QS_ERR_CUDA, "batch stream wait failed");
+  }
+  return QS_OK;
 }
 
 }  // extern "C"

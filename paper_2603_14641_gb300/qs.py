@@ -111,6 +111,7 @@ SIGNATURES = {
     "qs_batch_export_rows": (ctypes.c_int, [_vp, _u32, _vp, _u32, _vp]),
     "qs_batch_autotune": (ctypes.c_int, [_vp, _u32, ctypes.c_char_p, _vp]),
     "qs_batch_last_error": (ctypes.c_char_p, []),
+    "qs_batch_sample": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -602,6 +603,29 @@ class Batch:
         _bcheck(lib().qs_batch_record(ctypes.c_void_p(self.h), i, out.ctypes.data, self.meas[i]),
                 "qs_batch_record")
         return out[:self.meas[i]]
+
+    def sample(self, shots, seeds):
+        """Frame samples of every circuit (shots[i] shots, frame seed seeds[i]; 0
+        shots skips a circuit) from the last complete run: a list of device
+        tensors of shape (M_i, ceil(shots[i]/64)) int64 words (None where skipped).
+        Enqueued on the batch's stream."""
+        torch = self.torch
+        k = len(self.circuits)
+        sh = np.ascontiguousarray(shots, np.uint64)
+        sd = np.ascontiguousarray(seeds, np.uint64)
+        outs, ptrs = [], (ctypes.c_void_p * k)()
+        for i in range(k):
+            if sh[i] == 0:
+                outs.append(None)
+                continue
+            ow = (int(sh[i]) + 63) // 64
+            t = torch.empty((max(self.meas[i], 1), ow), dtype=torch.int64, device=self.device)
+            outs.append(t[:self.meas[i]])
+            ptrs[i] = t.data_ptr()
+        _bcheck(lib().qs_batch_sample(ctypes.c_void_p(self.h), sh.ctypes.data, sd.ctypes.data,
+                                      ctypes.cast(ptrs, ctypes.c_void_p)), "qs_batch_sample")
+        self._keep_samples = outs
+        return outs
 
     def export_rows(self, i: int, rows):
         n = self.circuits[i].n

@@ -13,7 +13,12 @@ built around its method:
   * continuous batching: every slot is a host worker with its own CUDA stream,
     so requests admitted while others are on the GPU run concurrently and their
     kernels overlap on the device; a request finishing frees its slot and its
-    memory for the next one;
+    memory for the next one. Small requests (under 1,024 qubits, no noise
+    channels) that wait together are served together: when a slot admits one,
+    it also takes the small requests queued right behind it (in arrival order,
+    within the memory budget, up to max_batch) and runs them as one batch --
+    all their reference shots in one persistent launch (qs_batch_run) and all
+    their shots in one sampling launch (qs_batch_sample);
   * results do not depend on the mix: each request owns its tableau and its
     coins and frames are keyed by (seed, shot, index), so a request's record is
     bit-identical alone and among others.
@@ -76,11 +81,20 @@ class Scheduler:
     """
 
     def __init__(self, slots: int, budget_bytes: int, footprint: Callable[[Request], int],
-                 execute: Callable[[Request, int, float, int], Result]):
+                 execute: Callable[[Request, int, float, int], Result],
+                 execute_batch: Optional[Callable] = None,
+                 batchable: Optional[Callable[[Request], bool]] = None, max_batch: int = 64):
         self.slots = slots
         self.budget = budget_bytes
         self.footprint = footprint
         self.execute = execute
+        # execute_batch(requests, slot, admit_s, footprints) -> [Result]; requests
+        # for which batchable() holds are grouped when they wait together
+        self.execute_batch = execute_batch
+        self.batchable = batchable
+        self.max_batch = max_batch
+        self.batches = 0          # batches of two or more requests run
+        self.batched_requests = 0
         self.cv = threading.Condition()
         self.pending: deque = deque()
         self.in_use = 0
@@ -111,8 +125,19 @@ class Scheduler:
                         if self.in_use + fp <= self.budget:
                             self.pending.popleft()
                             self.in_use += fp
+                            group, fps = [req], [fp]
+                            # small requests queued right behind join the head's batch
+                            if self.execute_batch is not None and self.batchable(req):
+                                while (self.pending and len(group) < self.max_batch
+                                       and self.batchable(self.pending[0])):
+                                    f2 = self.footprint(self.pending[0])
+                                    if self.in_use + f2 > self.budget:
+                                        break
+                                    group.append(self.pending.popleft())
+                                    fps.append(f2)
+                                    self.in_use += f2
                             self.peak_in_use = max(self.peak_in_use, self.in_use)
-                            self.active += 1
+                            self.active += len(group)
                             self.peak_active = max(self.peak_active, self.active)
                             admit = self.now()
                             break
@@ -120,17 +145,25 @@ class Scheduler:
                         return
                     self.cv.wait()
             try:
-                res = self.execute(req, slot, admit, fp)
-                res.done_s = self.now()
+                if len(group) > 1:
+                    results = self.execute_batch(group, slot, admit, fps)
+                    with self.cv:
+                        self.batches += 1
+                        self.batched_requests += len(group)
+                else:
+                    results = [self.execute(req, slot, admit, fp)]
+                done = self.now()
+                for res in results:
+                    res.done_s = done
                 with self.cv:
-                    self.results.append(res)
+                    self.results.extend(results)
             except BaseException as e:  # reported to the caller of run()
                 with self.cv:
                     self.errors.append(e)
             finally:
                 with self.cv:
-                    self.in_use -= fp
-                    self.active -= 1
+                    self.in_use -= sum(fps)
+                    self.active -= len(group)
                     self.cv.notify_all()
 
     def run(self, requests: List[Request], realtime: bool = True) -> List[Result]:
@@ -176,6 +209,39 @@ class GpuExecutor:
         c = req.circuit
         return footprint_bytes(c.n, c.n_gates, c.n_measurements, req.shots)
 
+    @staticmethod
+    def batchable(req: Request) -> bool:
+        """Small noiseless circuits run in the batch's persistent kernel."""
+        c = req.circuit
+        return c.n < 1024 and not any(op[0] == "noise" for op in c.ops)
+
+    def execute_batch(self, reqs: List[Request], slot: int, admit_s: float, fps) -> List[Result]:
+        """Serves requests together: reference shots in one persistent launch
+        (qs_batch_run), shots in one sampling launch (qs_batch_sample); the
+        coins are keyed (seed, 0) and the frames by seed + 1, as for a request
+        served alone, so the results are the same."""
+        torch, qs = self.torch, self.qs
+        stream = self.streams[slot]
+        with torch.cuda.device(self.device), torch.cuda.stream(stream):
+            b = qs.Batch([r.circuit for r in reqs], [r.seed for r in reqs], device=str(self.device),
+                         stream=stream)
+            b.run()
+            outs = b.sample([r.shots for r in reqs], [r.seed + 1 for r in reqs])
+            samples = []
+            for o in outs:
+                h = None
+                if self.keep_samples and o is not None:
+                    h = torch.empty(tuple(o.shape), dtype=torch.int64, pin_memory=True)
+                    h.copy_(o, non_blocking=True)
+                samples.append(h)
+            b.sync()
+            records = [b.record(i) for i in range(len(reqs))]
+            stream.synchronize()
+            b.close()
+        return [Result(r.rid, r.circuit.n, r.shots, r.arrival_s, admit_s, 0.0, f, rec,
+                       s.numpy().view(np.uint64) if s is not None else None)
+                for r, f, rec, s in zip(reqs, fps, records, samples)]
+
     def __call__(self, req: Request, slot: int, admit_s: float, fp: int) -> Result:
         torch, qs = self.torch, self.qs
         c = req.circuit
@@ -204,7 +270,10 @@ class GpuExecutor:
             fws = torch.empty(fb, dtype=torch.uint8, device=self.device)
             qs.qs_sim_sample(sim.sim, req.shots, req.seed + 1, out.data_ptr(), M * ow,
                              fws.data_ptr(), fb)
-            samples = out[:M].to("cpu", non_blocking=True) if self.keep_samples else None
+            samples = None
+            if self.keep_samples:  # to pinned host memory (the caching host allocator reuses it)
+                samples = torch.empty((M, ow), dtype=torch.int64, pin_memory=True)
+                samples.copy_(out[:M], non_blocking=True)
             record = sim.record()  # syncs the slot's stream and checks the device flags
             stream.synchronize()
             sim.close()
@@ -224,13 +293,17 @@ def summarize(results: List[Result], makespan_s: float) -> Dict[str, float]:
 
 
 def serve(requests: List[Request], slots: int = 8, budget_bytes: int = 64 << 30,
-          device: str = "cuda", keep_samples: bool = True, realtime: bool = True):
+          device: str = "cuda", keep_samples: bool = True, realtime: bool = True,
+          batching: bool = True, max_batch: int = 64):
     """Runs the request stream; returns (results sorted by id, summary, scheduler stats)."""
     ex = GpuExecutor(slots, device, keep_samples)
-    sch = Scheduler(slots, budget_bytes, ex.footprint, ex)
+    sch = Scheduler(slots, budget_bytes, ex.footprint, ex,
+                    execute_batch=ex.execute_batch if batching else None,
+                    batchable=ex.batchable, max_batch=max_batch)
     t = time.perf_counter()
     res = sch.run(requests, realtime=realtime)
     makespan = time.perf_counter() - t
     stats = {"peak_active": sch.peak_active, "peak_bytes": sch.peak_in_use,
-             "budget_bytes": budget_bytes, "slots": slots}
+             "budget_bytes": budget_bytes, "slots": slots, "batches": sch.batches,
+             "batched_requests": sch.batched_requests}
     return sorted(res, key=lambda r: r.rid), summarize(res, makespan), stats

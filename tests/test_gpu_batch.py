@@ -141,3 +141,36 @@ def test_batch_large_circuits_run_through_simulators():
         bx, bz, br = b.export_rows(i, rows)
         sx, sz, sr = s.export_rows(rows)
         assert np.array_equal(bx, sx) and np.array_equal(bz, sz) and np.array_equal(br, sr)
+
+
+def test_batched_sampling_matches_single_path_and_oracle():
+    """qs_batch_sample: every circuit's frame samples, drawn for all small
+    circuits in one launch (and through the worker simulators for n >= 1024),
+    equal qs_sim_sample of the circuit alone under the same seeds and the
+    oracle's Pauli-frame samples (Sec. 5), ragged shot counts included; a
+    circuit given 0 shots is skipped."""
+    circs = _mixed_batch(14, seed=5)
+    circs.append(C.random_circuit(1100, 8, 0.5, seed=9, measure_every=4, measure_frac=0.1))
+    seeds = [30 + i for i in range(len(circs))]
+    shots = [0 if i == 3 else [1, 64, 65, 200, 1000, 4097][i % 6] for i in range(len(circs))]
+    fseeds = [900 + i for i in range(len(circs))]
+    b = qs.Batch(circs, seeds, device="cuda:0")
+    with pytest.raises(qs.QsError):  # no complete run yet
+        b.sample(shots, fseeds)
+    b.run()
+    outs = b.sample(shots, fseeds)
+    b.sync()
+    for i, c in enumerate(circs):
+        if shots[i] == 0:
+            assert outs[i] is None
+            continue
+        got = outs[i].cpu().numpy().view(np.uint64)
+        s = qs.Simulator(c.n, device="cuda:0")
+        rec = s.run(c, seed=seeds[i])
+        want = s.sample(shots[i], seed=fseeds[i], on_device=False)
+        assert got.shape == want.shape and np.array_equal(got, want), f"circuit {i} (n={c.n})"
+        if c.n <= 700:
+            bits = np.unpackbits(got.view(np.uint8), axis=1, bitorder="little")
+            assert not bits[:, shots[i]:].any()
+            assert np.array_equal(bits[:, :shots[i]], O.frames(c, rec, shots[i], seed=fseeds[i]))
+        s.close()

@@ -53,3 +53,26 @@ def test_tight_budget_serialises_but_completes():
     biggest = max(ex.footprint(r) for r in reqs)
     res, summ, stats = serve.serve(reqs, slots=4, budget_bytes=biggest, device="cuda:0")
     assert len(res) == len(reqs) and stats["peak_bytes"] <= biggest
+
+
+def test_batched_small_requests_match_alone_and_oracle():
+    """Small requests that wait together are served as one batch (one
+    persistent launch for their reference shots, one launch for their shots);
+    each result equals the request served alone and the oracle's."""
+    rng = np.random.default_rng(11)
+    reqs = []
+    for i in range(10):
+        n = int(rng.integers(20, 1000))
+        circ = C.random_circuit(n, int(rng.integers(10, 40)), 0.5, seed=500 + i)
+        reqs.append(serve.Request(i, 0.0, circ, int(rng.integers(1, 3000)), seed=300 + i))
+    res, summ, stats = serve.serve(reqs, slots=1, budget_bytes=1 << 30, device="cuda:0")
+    assert stats["batches"] >= 1 and stats["batched_requests"] >= 2
+    for r in reqs:
+        alone, _, _ = serve.serve([serve.Request(r.rid, 0.0, r.circuit, r.shots, r.seed)], slots=1,
+                                  budget_bytes=1 << 30, device="cuda:0", batching=False)
+        a, m = alone[0], res[r.rid]
+        assert np.array_equal(a.record, m.record) and np.array_equal(a.samples, m.samples), r.rid
+        _, orec, _ = O.run_circuit(r.circuit, seed=r.seed, shot=0)
+        assert np.array_equal(m.record, orec)
+        bits = np.unpackbits(m.samples.view(np.uint8), axis=1, bitorder="little")
+        assert np.array_equal(bits[:, :r.shots], O.frames(r.circuit, orec, r.shots, seed=r.seed + 1))

@@ -97,3 +97,39 @@ def test_footprint_and_summary():
     s = summarize(res, makespan_s=10.0)
     assert s["requests"] == 100 and s["shots_per_s"] == 1000.0
     assert abs(s["p50_latency_s"] - 50.5) < 1e-9 and 99.0 < s["p99_latency_s"] <= 100.0
+
+
+def test_small_requests_waiting_together_are_batched_in_order():
+    """A slot that admits a batchable request also takes the batchable ones
+    queued right behind it (arrival order, within the budget and max_batch);
+    a non-batchable request ends the group; every request completes once."""
+    lock = threading.Lock()
+    groups = []
+
+    def execute(req, slot, admit, fp):
+        time.sleep(0.01)
+        with lock:
+            groups.append([req.rid])
+        return Result(req.rid, 0, req.shots, req.arrival_s, admit, 0.0, fp)
+
+    def execute_batch(reqs, slot, admit, fps):
+        time.sleep(0.01)
+        with lock:
+            groups.append([r.rid for r in reqs])
+        return [Result(r.rid, 0, r.shots, r.arrival_s, admit, 0.0, f) for r, f in zip(reqs, fps)]
+
+    # shots < 100: batchable; the budget lets at most 5 small ones share a group
+    sizes = [10, 20, 30, 500, 40, 50, 60, 70, 80, 90, 15, 700, 25]
+    sch = Scheduler(slots=1, budget_bytes=1000, footprint=lambda r: r.shots, execute=execute,
+                    execute_batch=execute_batch, batchable=lambda r: r.shots < 100, max_batch=4)
+    res = sch.run(_reqs(sizes), realtime=False)
+    assert sorted(r.rid for r in res) == list(range(len(sizes)))
+    flat = [rid for g in groups for rid in g]
+    assert flat == list(range(len(sizes)))  # one slot: FIFO order, no overtaking
+    for g in groups:
+        assert len(g) <= 4
+        if len(g) > 1:
+            assert all(sizes[r] < 100 for r in g)
+            assert g == list(range(g[0], g[0] + len(g)))  # consecutive in the queue
+    assert sch.batches >= 2 and sch.batched_requests >= 6
+    assert sch.peak_in_use <= 1000
