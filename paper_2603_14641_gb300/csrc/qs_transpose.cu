@@ -88,6 +88,36 @@ bit_transpose_kernel(const uint64_t *__restrict__ in, size_t in_stride, uint64_t
   }
 }
 
+// Branch-free form of transpose64 for the large-matrix kernel. In the round of
+// distance j the lower lane of a pair keeps its bits outside m << j and takes
+// its partner's bits m, shifted up by j; the upper lane keeps its bits outside m
+// and takes its partner's bits m << j, shifted down. Both are one bit-select
+// of a value shifted the lane's way, so no lane-dependent branch remains (the
+// two sides of that branch used to run one after the other).
+__device__ __forceinline__ void transpose64_sel(uint64_t &lo, uint64_t &hi, int lane) {
+  {
+    const uint64_t m = 0x00000000FFFFFFFFull;
+    uint64_t t = ((lo >> 32) ^ hi) & m;
+    lo ^= t << 32;
+    hi ^= t;
+  }
+  const uint64_t masks[5] = {0x0000FFFF0000FFFFull, 0x00FF00FF00FF00FFull, 0x0F0F0F0F0F0F0F0Full,
+                             0x3333333333333333ull, 0x5555555555555555ull};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const uint64_t m = masks[s];
+    const bool upper = (lane & j) != 0;
+    const uint64_t take = upper ? m : (m << j);  // bits taken from the partner
+    const uint64_t plo = __shfl_xor_sync(0xffffffffu, lo, j);
+    const uint64_t phi = __shfl_xor_sync(0xffffffffu, hi, j);
+    const uint64_t slo = upper ? (plo >> j) : (plo << j);
+    const uint64_t shi = upper ? (phi >> j) : (phi << j);
+    lo = (lo & ~take) | (slo & take);
+    hi = (hi & ~take) | (shi & take);
+  }
+}
+
 // Large matrices: a block of 512 threads covers 512 input rows x 16 input
 // words, so reads are 128-byte row segments and writes 64-byte ones (32-byte
 // segments reach only about a third of the HBM bandwidth). The tile is staged
@@ -109,13 +139,18 @@ bit_transpose_big_kernel(const uint64_t *__restrict__ in, size_t in_stride, size
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const size_t i0 = (size_t)blockIdx.y * kTR, j0 = (size_t)blockIdx.x * kTW;
   const int vr = (int)min((size_t)kTR, rows_in - i0), vw = (int)min((size_t)kTW, words_in - j0);
-  // 1: 16 words of a row per half warp (128-byte segments)
+  // 1: 16 words of a row per 8 threads, two words each (128-byte segments)
 #pragma unroll 4
-  for (int it = 0; it < kTR * kTW / kTT; ++it) {
-    const int idx = it * kTT + t, row = idx / kTW, w = idx % kTW;
-    uint64_t v = 0;
-    if (row < vr && w < vw) v = in[(i0 + row) * in_stride + j0 + w];
-    tl[tsw(row, w)] = v;
+  for (int it = 0; it < kTR * kTW / (2 * kTT); ++it) {
+    const int idx = it * kTT + t, row = idx / (kTW / 2), w = 2 * (idx % (kTW / 2));
+    ulonglong2 v = make_ulonglong2(0, 0);
+    if (row < vr && w + 1 < vw) {
+      v = *reinterpret_cast<const ulonglong2 *>(in + (i0 + row) * in_stride + j0 + w);
+    } else if (row < vr && w < vw) {
+      v.x = in[(i0 + row) * in_stride + j0 + w];
+    }
+    tl[tsw(row, w)] = v.x;
+    tl[tsw(row, w + 1)] = v.y;
   }
   __syncthreads();
   // 2: 256 sub-tiles (16 row groups x 16 words), 8 per warp
@@ -123,7 +158,7 @@ bit_transpose_big_kernel(const uint64_t *__restrict__ in, size_t in_stride, size
   for (int k = 0; k < (kTR / 64) * kTW / (kTT / 32); ++k) {
     const int st = warp * ((kTR / 64) * kTW / (kTT / 32)) + k, rt = st / kTW, w = st % kTW;
     uint64_t lo = tl[tsw(64 * rt + lane, w)], hi = tl[tsw(64 * rt + lane + 32, w)];
-    transpose64(lo, hi, lane);
+    transpose64_sel(lo, hi, lane);
     // now lo = output row 64 w + lane, word rt; hi = output row 64 w + lane + 32
     tl[tsw(64 * rt + lane, w)] = lo;
     tl[tsw(64 * rt + lane + 32, w)] = hi;
