@@ -52,6 +52,7 @@ struct Op {
   int noise_kind = 0;            // kNoise: QS_NOISE_*
   uint64_t thr = 0;              // kNoise: a shot fires iff its 32-bit draw u < thr
   uint64_t ordinal = 0;          // kNoise: index among the noise ops (the draw's e)
+  uint64_t dev_off = 0;          // kNoise: offset of its targets in the sim's noise buffer (words)
 };
 
 constexpr int kRing = 4;
@@ -132,6 +133,11 @@ struct qs_sim {
   void *blk = nullptr;  // scratch of the blocked measurement
   bool resumed = false; // state restored by qs_sim_tableau_import: no op log from |0...0>
   std::unique_ptr<KernelTimer> timer;  // qs_sim_set_timing
+  // every noise op's targets, uploaded once for qs_sim_sample's replays (valid
+  // while noise_dev_ops equals n_noise; it grows, never shrinks, until destroy)
+  uint32_t *noise_dev = nullptr;
+  size_t noise_dev_words = 0;
+  uint64_t noise_dev_ops = 0;
 };
 
 namespace {
@@ -375,6 +381,7 @@ int qs_sim_destroy(qs_sim *s) {
     if (s->hstage[i]) cudaFreeHost(s->hstage[i]);
   }
   if (s->owns_ws && s->ws) cudaFree(s->ws);
+  if (s->noise_dev) cudaFree(s->noise_dev);
   delete s;
   return QS_OK;
 }
@@ -409,6 +416,7 @@ int qs_sim_reset(qs_sim *s, const uint8_t *initstate) {
   s->n_noise = 0;
   s->ops.clear();
   s->resumed = false;
+  s->noise_dev_ops = 0;  // the buffer is kept for the next program's noise ops
   return QS_OK;
 }
 
@@ -754,6 +762,53 @@ static int replay_noise(qs_sim *s, const Op &op, uint64_t *FX, uint64_t *FZ, uin
   return QS_OK;
 }
 
+// Uploads the targets of every noise op of the op log into one device buffer
+// (once per change of the op log), so that replays launch straight from it.
+static int upload_noise_targets(qs_sim *s) {
+  if (s->n_noise == 0 || s->noise_dev_ops == s->n_noise) return QS_OK;
+  size_t words = 0;
+  for (const Op &op : s->ops)
+    if (op.kind == Op::kNoise) words += op.qubits.size();
+  std::vector<uint32_t> host(std::max<size_t>(words, 1));
+  size_t off = 0;
+  for (Op &op : s->ops)
+    if (op.kind == Op::kNoise) {
+      op.dev_off = off;
+      if (!op.qubits.empty()) memcpy(host.data() + off, op.qubits.data(), op.qubits.size() * 4);
+      off += op.qubits.size();
+    }
+  if (words > s->noise_dev_words) {
+    if (s->noise_dev) {
+      QS_CUDA(s, cudaStreamSynchronize(s->stream));  // earlier replays may still read it
+      QS_CUDA(s, cudaFree(s->noise_dev));
+      s->noise_dev = nullptr;
+      s->noise_dev_words = 0;
+    }
+    cudaError_t e = cudaMalloc(&s->noise_dev, words * 4);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      s->noise_dev = nullptr;
+      return fail(QS_ERR_OOM, "device buffer of the noise targets");
+    }
+    s->noise_dev_words = words;
+  }
+  QS_CUDA(s, cudaMemcpyAsync(s->noise_dev, host.data(), words * 4, cudaMemcpyHostToDevice, s->stream));
+  QS_CUDA(s, cudaStreamSynchronize(s->stream));  // the host copy goes out of scope
+  s->noise_dev_ops = s->n_noise;
+  return QS_OK;
+}
+
+// One noise op straight from the uploaded targets.
+static int replay_noise_dev(qs_sim *s, const Op &op, uint64_t *FX, uint64_t *FZ, uint32_t fw, uint32_t ow,
+                            uint64_t seed) {
+  const uint32_t per = op.noise_kind == QS_NOISE_DEPOLARIZE2 ? 2 : 1;
+  const uint32_t total = (uint32_t)op.qubits.size() / per;
+  QS_CUDA(s, launch_frame_noise(FX, FZ, fw, ow, s->noise_dev + op.dev_off, total, 0, op.noise_kind, op.thr,
+                                op.ordinal, seed, s->stream));
+  if (op.thr && total) s->launches += 1;
+  return QS_OK;
+}
+
 static size_t sample_bytes(const qs_sim *s, uint64_t shots, uint64_t *fw_out, uint64_t *ow_out) {
   const uint64_t ow = (shots + 63) / 64;
   const uint64_t fw = (ow + 3) / 4 * 4;
@@ -819,6 +874,7 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
   uint64_t *dout = reinterpret_cast<uint64_t *>(b + c.take((size_t)std::max<uint64_t>(1, M) * ow * 8));
   const bool out_dev = M ? is_device_ptr(record) : true;
   uint64_t *out = out_dev ? record : dout;
+  if ((rc = upload_noise_targets(s))) return rc;
   tbegin(s->d.timer, QS_TIME_SAMPLE, s->stream);
   QS_CUDA(s, launch_frame_init(FX, FZ, n, (uint32_t)fw, seed, s->stream));
   s->launches += 1;
@@ -839,7 +895,7 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
                                op.ptr.size() - 1, false)))
         return rc;
     } else if (op.kind == Op::kNoise) {
-      if ((rc = replay_noise(s, op, FX, FZ, (uint32_t)fw, (uint32_t)ow, seed))) return rc;
+      if ((rc = replay_noise_dev(s, op, FX, FZ, (uint32_t)fw, (uint32_t)ow, seed))) return rc;
     } else {
       // measurement window: split into runs of distinct qubits (Sec. 5 processes
       // the measurements of one window in parallel)
@@ -1026,6 +1082,7 @@ int qs_sim_tableau_import(qs_sim *s, int layout, const void *src, size_t src_byt
   s->n_meas = record_count;
   s->n_noise = 0;
   s->ops.clear();
+  s->noise_dev_ops = 0;
   s->resumed = true;
   return QS_OK;
 }

@@ -105,3 +105,36 @@ def test_bad_noise_arguments_are_rejected():
     sim.measure(np.array([1, 2, 3], np.uint32), seed=0)
     w = sim.sample(64, 1, on_device=False)
     assert w.shape == (3, 1)
+
+
+def test_noise_targets_follow_the_op_log():
+    """Sampling keeps every noise op's targets on the device between calls: a
+    program that grows after a sample, and a new program after reset (fewer
+    and then more targets than the buffer holds), still sample bit-exact."""
+    n, shots = 120, 200
+    base = C.random_circuit(n, 8, 0.5, seed=21, measure_every=4, measure_frac=0.3,
+                            final_measure_all=False)
+    first = C.with_circuit_noise(base, 0.03, 0.05)
+    rng = np.random.default_rng(5)
+    tail = [("noise", C.DEPOLARIZE2, 0.2, rng.permutation(n)[:80].astype(np.uint32)),
+            ("noise", C.NOISE_Y, 0.4, rng.permutation(n)[:50].astype(np.uint32)),
+            ("measure", np.arange(n, dtype=np.uint32))]
+    whole = C.Circuit(n=n, gates=first.gates, layer_ptr=first.layer_ptr,
+                      ops=list(first.ops) + tail)
+    sim = qs.Simulator(n, device="cuda:0")
+    for circ, ops in ((first, first.ops), (whole, tail)):
+        rec = sim.run(C.Circuit(n=n, gates=first.gates, layer_ptr=first.layer_ptr, ops=ops), seed=2)
+        _, orec, _ = O.run_circuit(circ, seed=2)
+        assert np.array_equal(rec, orec)
+        words = sim.sample(shots, 7, on_device=False)
+        assert np.array_equal(_bits(words, shots), O.frames(circ, orec, shots, 7))
+    for p, depth in ((0.1, 3), (0.02, 14)):
+        circ = C.with_circuit_noise(C.random_circuit(n, depth, 0.5, seed=depth, measure_every=3,
+                                                     measure_frac=0.4, final_measure_all=True),
+                                    p, p)
+        sim.reset()
+        rec = sim.run(circ, seed=4)
+        _, orec, _ = O.run_circuit(circ, seed=4)
+        assert np.array_equal(rec, orec)
+        words = sim.sample(shots, 3, on_device=False)
+        assert np.array_equal(_bits(words, shots), O.frames(circ, orec, shots, 3))
