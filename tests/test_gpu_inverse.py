@@ -128,3 +128,22 @@ def test_inverse_mode_refusals():
         chp.qubit_signs()
     assert e.value.code == -6
     sim.sync()
+
+
+@pytest.mark.parametrize("n,seed", [(64, 1), (130, 2), (300, 3)])
+def test_inverse_mode_holds_the_chp_oracles_stabilizer_group(n, seed):
+    """The canonical stabilizer group (reduced row echelon form with signs)
+    of the GPU's inverse tableau equals that of the CHP oracle after gates and
+    measurements under the same keyed coins."""
+    from tests import stabilizer_canon as SC
+    circ = C.gate_mix_circuit(n, 18, seed=seed + 90, measure_every=4, measure_frac=0.3)
+    sim = _sim(n)
+    rec = sim.run(circ, seed=seed * 7)
+    o, orec, _ = O.run_circuit(circ, seed=seed * 7)
+    assert np.array_equal(rec, orec)
+    x, z, _ = sim.export()
+    ss, sd = sim.qubit_signs()
+    got = SC.stabilizer_group_of_inverse(x, z, ss, sd)
+    want = SC.stabilizer_group_of_chp(*o.get())
+    assert len(want[2]) == n and SC.same_group(got, want)
+    sim.sync()
