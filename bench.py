@@ -1001,7 +1001,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n180k",
                     choices=sorted(WORKLOADS) + ["batch", "serve", "l2probe"])
-    ap.add_argument("--serve-count", type=int, default=24)
+    ap.add_argument("--serve-count", type=int, default=64)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=int, default=96)
     ap.add_argument("--batch-count", type=int, default=512)

@@ -1257,6 +1257,7 @@ int qs_batch_export_rows(qs_batch *b, uint32_t circuit, const uint32_t *rows, ui
   Dev d{};
   d.L = make_layout(C.n);
   d.X = C.X; d.Z = C.Z; d.RX = C.RX; d.RZ = C.RZ;
+  d.err = b->d_err;
   cudaError_t e = launch_to_rows(d, b->stream);
   std::vector<uint64_t> S(C.cs);
   if (e == cudaSuccess)

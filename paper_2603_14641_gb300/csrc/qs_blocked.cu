@@ -452,20 +452,26 @@ __global__ void __launch_bounds__(64) blk_signs_kernel(const uint64_t *__restric
 
 // phase 3: block = one chunk of kCW (32) column words x a range of rows.
 // The XOR of any subset of the 64 V rows is assembled from tables of XOR
-// combinations of consecutive steps (the "Four Russians" method): steps are cut
-// into 12 groups of 5 and one of 4, and T[g][c] = XOR of V[5g + b] over the bits
-// b of c, built once per block in shared memory (200 KB), so a row needs 13
-// lookups. A warp handles one row (lane = column word, x and z side by side in
-// one 16-byte table entry, 512 bytes per entry); a row segment is 256 contiguous
-// bytes of each matrix, the shortest that keeps HBM fully efficient. Each warp
-// keeps the next two rows' loads in flight while it works on the current one;
-// the row loop is unrolled by three so the in-flight rows rotate through
-// registers without copies.
-constexpr int kGroups = 13, kGroupBits = 5;
-constexpr int kEntries = 12 * 32 + 16;  // 400 table entries of kCW (x, z) word pairs
+// combinations of consecutive steps (the "Four Russians" method), built once
+// per block: T[g][c] = XOR of V[first step of g + b] over the bits b of c. A
+// warp handles one row (lane = column word, x and z side by side in one
+// 16-byte entry, 512 bytes per entry over the warp); a row segment is 256
+// contiguous bytes of each matrix, the shortest that keeps HBM fully
+// efficient. Each warp keeps the next two rows' loads in flight while it
+// works on the current one; the row loop is unrolled by three so the
+// in-flight rows rotate through registers without copies.
+//
+// The tables live in two memories of the SM. Steps 0..43 use shared memory:
+// seven groups of 6 steps and one of 2 (452 entries, 226 KB). Steps 44..63
+// use tensor memory (TMEM, 512 columns x 128 lanes of 32 bits): four groups
+// of 5 steps. TMEM lane l of each 32-lane quarter holds column word l of the
+// chunk and every quarter holds the same four tables (a warp reads only the
+// lanes of its quarter, warp mod 4), so an entry is 4 columns (x lo, x hi,
+// z lo, z hi) and group t, pattern p sits at columns 128 t + 4 p. A row costs
+// 8 shared-memory lookups (32 wavefronts; 13 lookups and 52 wavefronts with
+// 5-step groups in shared memory alone, which bounded the pass on the
+// shared-memory pipe) and 4 TMEM loads on the tensor-memory read path.
 constexpr int kEntryBytes = kCW * 16;   // 512
-__host__ __device__ constexpr int group_base(int g) { return 32 * g; }
-__host__ __device__ constexpr int group_size(int g) { return g < 12 ? 32 : 16; }
 
 struct ApplyRow {
   int32_t b;
@@ -520,12 +526,19 @@ __device__ __forceinline__ void acc3(uint4 &a, const uint4 &p, const uint4 &q) {
   a.w = xor3(a.w, p.w, q.w);
 }
 
-// byte offset (pattern * 512) of the entry of group g, from the 32-bit halves of M_r
+constexpr int kSmemGroups = 8;            // shared-memory groups (steps 0..43)
+constexpr int kSmemEntries = 7 * 64 + 4;  // 452 entries of 512 bytes
+constexpr int kTmemStep0 = 44;            // first step held in TMEM
+constexpr uint32_t kTmemCols = 512;       // all of the SM's tensor memory
+__host__ __device__ constexpr int smem_group_bits(int g) { return g < 7 ? 6 : 2; }
+__host__ __device__ constexpr int smem_group_base(int g) { return 64 * g; }
+
+// byte offset (pattern * 512) of shared group g (6 steps from 6 g; group 7: steps 42, 43)
 template <int g>
 __device__ __forceinline__ uint32_t pat_off(uint32_t lo, uint32_t hi) {
-  constexpr int sh = kGroupBits * g;
-  constexpr uint32_t mask = (uint32_t)(group_size(g) - 1) * kEntryBytes;
-  if constexpr (sh + kGroupBits <= 32) {
+  constexpr int sh = 6 * g, nb = smem_group_bits(g);
+  constexpr uint32_t mask = (uint32_t)((1 << nb) - 1) * kEntryBytes;
+  if constexpr (sh + nb <= 32) {
     if constexpr (sh >= 9) return (lo >> (sh - 9)) & mask;
     else return (lo << (9 - sh)) & mask;
   } else if constexpr (sh >= 32) {
@@ -536,18 +549,47 @@ __device__ __forceinline__ uint32_t pat_off(uint32_t lo, uint32_t hi) {
   }
 }
 
-// table entry of group g for this lane: (x lo, x hi, z lo, z hi)
+// shared table entry of group g for this lane: (x lo, x hi, z lo, z hi)
 template <int g>
 __device__ __forceinline__ uint4 tab(const char *tl, uint32_t lo, uint32_t hi) {
-  return *reinterpret_cast<const uint4 *>(tl + group_base(g) * kEntryBytes + pat_off<g>(lo, hi));
+  return *reinterpret_cast<const uint4 *>(tl + smem_group_base(g) * kEntryBytes + pat_off<g>(lo, hi));
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint4 &v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(taddr));
+}
+
+// waits for this thread's TMEM loads; the operands tie the loaded registers
+// to the wait so that no use is scheduled before it
+__device__ __forceinline__ void tmem_wait_ld(uint4 &a, uint4 &b, uint4 &c, uint4 &d) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a.x), "+r"(a.y), "+r"(a.z), "+r"(a.w), "+r"(b.x), "+r"(b.y), "+r"(b.z), "+r"(b.w),
+                 "+r"(c.x), "+r"(c.y), "+r"(c.z), "+r"(c.w), "+r"(d.x), "+r"(d.y), "+r"(d.z), "+r"(d.w)
+               :
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint4 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v.x),
+               "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
 template <typename Idx>
 __device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t r, uint32_t nrows, uint64_t *RX,
-                                          uint64_t *RZ, Idx off, bool ok, uint32_t word,
-                                          const uint32_t *qubits, const uint64_t *VX,
-                                          const uint64_t *VZ, uint32_t rs, uint32_t lane,
-                                          const char *tl, int32_t *Tp, uint64_t tp0) {
+                                             uint64_t *RZ, Idx off, bool ok, uint32_t word,
+                                             const uint32_t *qubits, const uint64_t *VX,
+                                             const uint64_t *VZ, uint32_t rs, uint32_t lane,
+                                             const char *tl, uint32_t tq, int32_t *Tp, uint64_t tp0) {
   if (r >= nrows) return;  // uniform over the warp
   uint2 *px = reinterpret_cast<uint2 *>(RX), *pz = reinterpret_cast<uint2 *>(RZ);
   if (a.b >= kBasePivot) {  // pivot row of step j: +-Z_q (sign set by blk_rows_kernel)
@@ -565,22 +607,30 @@ __device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t r, uint32_
     xb = reinterpret_cast<const uint2 *>(VX)[(uint64_t)a.b * rs + word];
     zb = reinterpret_cast<const uint2 *>(VZ)[(uint64_t)a.b * rs + word];
   }
-  // branch-free: pattern 0 is a zero entry, so all 13 loads can be in flight together
   const uint32_t lo = a.lo, hi = a.hi;
+  // steps 44..63 = bits 12..31 of hi: TMEM group t holds bits 12 + 5 t ..
+  uint4 m0, m1, m2, m3;
+  tmem_ld4(tq + 4 * ((hi >> 12) & 31), m0);
+  tmem_ld4(tq + 128 + 4 * ((hi >> 17) & 31), m1);
+  tmem_ld4(tq + 256 + 4 * ((hi >> 22) & 31), m2);
+  tmem_ld4(tq + 384 + 4 * (hi >> 27), m3);
   uint4 acc = tab<0>(tl, lo, hi);
   acc3(acc, tab<1>(tl, lo, hi), tab<2>(tl, lo, hi));
   acc3(acc, tab<3>(tl, lo, hi), tab<4>(tl, lo, hi));
   acc3(acc, tab<5>(tl, lo, hi), tab<6>(tl, lo, hi));
-  acc3(acc, tab<7>(tl, lo, hi), tab<8>(tl, lo, hi));
-  acc3(acc, tab<9>(tl, lo, hi), tab<10>(tl, lo, hi));
-  acc3(acc, tab<11>(tl, lo, hi), tab<12>(tl, lo, hi));
+  const uint4 s7 = tab<7>(tl, lo, hi);
+  tmem_wait_ld(m0, m1, m2, m3);
+  acc3(acc, s7, m0);
+  acc3(acc, m1, m2);
+  acc.x ^= m3.x;
+  acc.y ^= m3.y;
+  acc.z ^= m3.z;
+  acc.w ^= m3.w;
   const uint2 xf = make_uint2(xb.x ^ acc.x, xb.y ^ acc.y), zf = make_uint2(zb.x ^ acc.z, zb.y ^ acc.w);
   if (ok) {
     px[off] = xf;
     pz[off] = zf;
   }
-  // t = |x_b & z_b| - |x_f & z_f| summed over the chunk, c = parity of z_acc . x_b;
-  // one warp reduction of 64 t + c (0 <= sum of c <= 32)
   const int t = __popc(xb.x & zb.x) + __popc(xb.y & zb.y) - __popc(xf.x & zf.x) - __popc(xf.y & zf.y);
   const int c = (__popc(acc.z & xb.x) + __popc(acc.w & xb.y)) & 1;
   const int v = __reduce_add_sync(0xffffffffu, 64 * t + c);
@@ -588,69 +638,118 @@ __device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t r, uint32_
 }
 
 template <typename Idx>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024, 1)
 blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t rs, uint32_t nrows,
-                 const uint32_t *__restrict__ qubits, const uint64_t *__restrict__ VX,
-                 const uint64_t *__restrict__ VZ, const uint64_t *__restrict__ M,
-                 const int32_t *__restrict__ base, int32_t *__restrict__ Tp, const BlkState *st) {
-  extern __shared__ ulonglong2 T[];  // [kEntries][kCW] of (x word, z word)
+                    const uint32_t *__restrict__ qubits, const uint64_t *__restrict__ VX,
+                    const uint64_t *__restrict__ VZ, const uint64_t *__restrict__ M,
+                    const int32_t *__restrict__ base, int32_t *__restrict__ Tp, const BlkState *st) {
+  extern __shared__ ulonglong2 T[];  // [kSmemEntries][kCW] of (x word, z word)
+  __shared__ uint32_t s_tmem;
   const int L = st->len;
   const uint32_t u0 = blockIdx.x * kCW;  // first column word of the chunk
   const uint32_t nw = min((uint32_t)kCW, rs - u0);
-  // table: entry 0 of a group is zero; entry c = entry (c with its lowest bit
-  // cleared) ^ V[5g + lowest bit of c]
-  for (int i = threadIdx.x; i < kGroups * kCW; i += blockDim.x) {
-    const int g = i / kCW, w = i % kCW;
-    ulonglong2 vv[kGroupBits];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {  // the whole TMEM of the SM: one block per SM (the tables fill shared memory)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&s_tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // shared tables: entry 0 of a group is zero; entry c = entry (c with its
+  // lowest bit cleared) ^ V[first step of g + lowest bit of c]
+  for (int i = threadIdx.x; i < kSmemGroups * kCW; i += blockDim.x) {
+    const int g = i / kCW, w = i % kCW, nb = smem_group_bits(g), e0 = smem_group_base(g);
+    ulonglong2 vv[6];
 #pragma unroll
-    for (int b = 0; b < kGroupBits; ++b) {
-      const int s = kGroupBits * g + b;
+    for (int b = 0; b < 6; ++b) {
+      const int s = 6 * g + b;
       vv[b] = make_ulonglong2(0, 0);
-      if (s < L && s < 64 && (uint32_t)w < nw)
+      if (b < nb && s < L && (uint32_t)w < nw)
         vv[b] = make_ulonglong2(VX[(uint64_t)s * rs + u0 + w], VZ[(uint64_t)s * rs + u0 + w]);
     }
-    const int e0 = group_base(g), ne = group_size(g);
     T[e0 * kCW + w] = make_ulonglong2(0, 0);
 #pragma unroll
-    for (int c = 1; c < 32; ++c) {
-      if (c >= ne) break;
-      const int lb = (c & 1) ? 0 : (c & 2) ? 1 : (c & 4) ? 2 : (c & 8) ? 3 : 4, prev = c & (c - 1);
+    for (int c = 1; c < 64; ++c) {
+      if (c >= (1 << nb)) break;
+      const int lb = (c & 1) ? 0 : (c & 2) ? 1 : (c & 4) ? 2 : (c & 8) ? 3 : (c & 16) ? 4 : 5,
+                prev = c & (c - 1);
       const ulonglong2 pv = T[(e0 + prev) * kCW + w];
       T[(e0 + c) * kCW + w] = make_ulonglong2(pv.x ^ vv[lb].x, pv.y ^ vv[lb].y);
     }
   }
+  tc_fence_before();
   __syncthreads();
-  if (L == 0) return;
-  const uint32_t lane = threadIdx.x & 31;
-  const bool ok = lane < nw;
-  const uint32_t word = u0 + lane;
-  const char *tl = reinterpret_cast<const char *>(T) + lane * 16;
-  const uint32_t units = gridDim.y * (blockDim.x >> 5);
-  const Idx step = (Idx)units * rs;
-  const uint64_t tp0 = (uint64_t)blockIdx.x * nrows;
-  uint32_t r = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  Idx off = (Idx)r * rs + word;
-  // unrolled by three so the rows in flight rotate through registers without
-  // copies; each row's pattern is loaded one stage before its words
-  ApplyRow a0, a1, a2;
-  ApplyMeta mn;
-  apply_meta(mn, r, nrows, M, base);
-  apply_fetch<Idx>(a0, mn, RX, RZ, off, ok);
-  apply_meta(mn, r + units, nrows, M, base);
-  apply_fetch<Idx>(a1, mn, RX, RZ, off + step, ok);
-  apply_meta(mn, r + 2 * units, nrows, M, base);
-  for (; r < nrows; r += 3 * units, off += 3 * step) {
-    apply_fetch<Idx>(a2, mn, RX, RZ, off + 2 * step, ok);
-    apply_meta(mn, r + 3 * units, nrows, M, base);
-    apply_row<Idx>(a0, r, nrows, RX, RZ, off, ok, word, qubits, VX, VZ, rs, lane, tl, Tp, tp0);
-    apply_fetch<Idx>(a0, mn, RX, RZ, off + 3 * step, ok);
-    apply_meta(mn, r + 4 * units, nrows, M, base);
-    apply_row<Idx>(a1, r + units, nrows, RX, RZ, off + step, ok, word, qubits, VX, VZ, rs, lane, tl, Tp,
-                   tp0);
-    apply_fetch<Idx>(a1, mn, RX, RZ, off + 4 * step, ok);
-    apply_meta(mn, r + 5 * units, nrows, M, base);
-    apply_row<Idx>(a2, r + 2 * units, nrows, RX, RZ, off + 2 * step, ok, word, qubits, VX, VZ, rs, lane,
-                   tl, Tp, tp0);
+  tc_fence_after();
+  const uint32_t tq = s_tmem + ((32u * (warp & 3)) << 16);  // lane quarter of this warp
+  if (warp < 4) {
+    // TMEM tables of this quarter: group t, entries in Gray-code order so that
+    // each differs from the previous one by one V row
+    for (int t = 0; t < 4; ++t) {
+      uint4 v[5];
+#pragma unroll
+      for (int b = 0; b < 5; ++b) {
+        const int s = kTmemStep0 + 5 * t + b;
+        v[b] = make_uint4(0, 0, 0, 0);
+        if (s < L && lane < nw) {
+          const uint2 x = reinterpret_cast<const uint2 *>(VX)[(uint64_t)s * rs + u0 + lane];
+          const uint2 z = reinterpret_cast<const uint2 *>(VZ)[(uint64_t)s * rs + u0 + lane];
+          v[b] = make_uint4(x.x, x.y, z.x, z.y);
+        }
+      }
+      uint4 e = make_uint4(0, 0, 0, 0);
+      tmem_st4(tq + 128 * t, e);
+#pragma unroll
+      for (int i = 1; i < 32; ++i) {
+        const int b = __ffs(i) - 1;
+        e.x ^= v[b].x;
+        e.y ^= v[b].y;
+        e.z ^= v[b].z;
+        e.w ^= v[b].w;
+        tmem_st4(tq + 128 * t + 4 * (i ^ (i >> 1)), e);
+      }
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (L > 0) {
+    const bool ok = lane < nw;
+    const uint32_t word = u0 + lane;
+    const char *tl = reinterpret_cast<const char *>(T) + lane * 16;
+    const uint32_t units = gridDim.y * (blockDim.x >> 5);
+    const Idx step = (Idx)units * rs;
+    const uint64_t tp0 = (uint64_t)blockIdx.x * nrows;
+    uint32_t r = blockIdx.y * (blockDim.x >> 5) + warp;
+    Idx off = (Idx)r * rs + word;
+    ApplyRow a0, a1, a2;
+    ApplyMeta mn;
+    apply_meta(mn, r, nrows, M, base);
+    apply_fetch<Idx>(a0, mn, RX, RZ, off, ok);
+    apply_meta(mn, r + units, nrows, M, base);
+    apply_fetch<Idx>(a1, mn, RX, RZ, off + step, ok);
+    apply_meta(mn, r + 2 * units, nrows, M, base);
+    for (; r < nrows; r += 3 * units, off += 3 * step) {
+      apply_fetch<Idx>(a2, mn, RX, RZ, off + 2 * step, ok);
+      apply_meta(mn, r + 3 * units, nrows, M, base);
+      apply_row<Idx>(a0, r, nrows, RX, RZ, off, ok, word, qubits, VX, VZ, rs, lane, tl, tq, Tp, tp0);
+      apply_fetch<Idx>(a0, mn, RX, RZ, off + 3 * step, ok);
+      apply_meta(mn, r + 4 * units, nrows, M, base);
+      apply_row<Idx>(a1, r + units, nrows, RX, RZ, off + step, ok, word, qubits, VX, VZ, rs, lane, tl,
+                        tq, Tp, tp0);
+      apply_fetch<Idx>(a1, mn, RX, RZ, off + 4 * step, ok);
+      apply_meta(mn, r + 5 * units, nrows, M, base);
+      apply_row<Idx>(a2, r + 2 * units, nrows, RX, RZ, off + 2 * step, ok, word, qubits, VX, VZ, rs,
+                        lane, tl, tq, Tp, tp0);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(kTmemCols)
+                 : "memory");
   }
 }
 
@@ -734,7 +833,7 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   uint64_t *VZ = reinterpret_cast<uint64_t *>(take(64ull * L.rs * 8));
   BlkState *st = reinterpret_cast<BlkState *>(take(sizeof(BlkState)));
   const unsigned rb = (unsigned)((L.nrows + 255) / 256);
-  const size_t smem = (size_t)kEntries * kEntryBytes;
+  const size_t smem = (size_t)kSmemEntries * kEntryBytes;
   cudaError_t ea = once_per_device(g_apply_attr_set, [&]() {
     cudaError_t e = cudaFuncSetAttribute(blk_apply_kernel<uint32_t>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -768,9 +867,9 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
                                                                               VZ, st);
   blk_signs_kernel<<<1, 64, 0, s>>>(d.S, st, d.err);
   tend(d.timer, QS_TIME_BLK_PIVOT_ROWS, s);
-  // about 8 waves of one block per SM (the table takes 200 KB of shared memory),
-  // but at least 512 rows per block so that building the 200 KB table stays
-  // small next to the rows it serves
+  // about 8 waves of one block per SM (the tables take 226 KB of shared
+  // memory and all of TMEM), but at least 512 rows per block so that building
+  // the tables stays small next to the rows they serve
   const uint32_t rows_y = std::max<uint32_t>(
       1, (uint32_t)std::min<uint64_t>(((uint64_t)d.sms * 8 + chunks - 1) / chunks, L.nrows / 512));
   tbegin(d.timer, QS_TIME_BLK_APPLY, s);
