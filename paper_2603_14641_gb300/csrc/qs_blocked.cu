@@ -549,10 +549,12 @@ __device__ __forceinline__ uint32_t pat_off(uint32_t lo, uint32_t hi) {
   }
 }
 
-// shared table entry of group g for this lane: (x lo, x hi, z lo, z hi)
+// shared table entry of group g for this lane: (x lo, x hi, z lo, z hi); the
+// pattern's byte offset is a multiple of 512 and the lane's (16 lane) is
+// below 512, so one OR joins them
 template <int g>
-__device__ __forceinline__ uint4 tab(const char *tl, uint32_t lo, uint32_t hi) {
-  return *reinterpret_cast<const uint4 *>(tl + smem_group_base(g) * kEntryBytes + pat_off<g>(lo, hi));
+__device__ __forceinline__ uint4 tab(const char *tb, uint32_t lane16, uint32_t lo, uint32_t hi) {
+  return *reinterpret_cast<const uint4 *>(tb + smem_group_base(g) * kEntryBytes + (pat_off<g>(lo, hi) | lane16));
 }
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint4 &v) {
@@ -589,7 +591,7 @@ __device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t r, uint32_
                                              uint64_t *RZ, Idx off, bool ok, uint32_t word,
                                              const uint32_t *qubits, const uint64_t *VX,
                                              const uint64_t *VZ, uint32_t rs, uint32_t lane,
-                                             const char *tl, uint32_t tq, int32_t *Tp, uint64_t tp0) {
+                                             const char *tb, uint32_t tq, int32_t *Tp, uint64_t tp0) {
   if (r >= nrows) return;  // uniform over the warp
   uint2 *px = reinterpret_cast<uint2 *>(RX), *pz = reinterpret_cast<uint2 *>(RZ);
   if (a.b >= kBasePivot) {  // pivot row of step j: +-Z_q (sign set by blk_rows_kernel)
@@ -614,11 +616,12 @@ __device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t r, uint32_
   tmem_ld4(tq + 128 + 4 * ((hi >> 17) & 31), m1);
   tmem_ld4(tq + 256 + 4 * ((hi >> 22) & 31), m2);
   tmem_ld4(tq + 384 + 4 * (hi >> 27), m3);
-  uint4 acc = tab<0>(tl, lo, hi);
-  acc3(acc, tab<1>(tl, lo, hi), tab<2>(tl, lo, hi));
-  acc3(acc, tab<3>(tl, lo, hi), tab<4>(tl, lo, hi));
-  acc3(acc, tab<5>(tl, lo, hi), tab<6>(tl, lo, hi));
-  const uint4 s7 = tab<7>(tl, lo, hi);
+  const uint32_t l16 = lane * 16;
+  uint4 acc = tab<0>(tb, l16, lo, hi);
+  acc3(acc, tab<1>(tb, l16, lo, hi), tab<2>(tb, l16, lo, hi));
+  acc3(acc, tab<3>(tb, l16, lo, hi), tab<4>(tb, l16, lo, hi));
+  acc3(acc, tab<5>(tb, l16, lo, hi), tab<6>(tb, l16, lo, hi));
+  const uint4 s7 = tab<7>(tb, l16, lo, hi);
   tmem_wait_ld(m0, m1, m2, m3);
   acc3(acc, s7, m0);
   acc3(acc, m1, m2);
@@ -632,7 +635,7 @@ __device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t r, uint32_
     pz[off] = zf;
   }
   const int t = __popc(xb.x & zb.x) + __popc(xb.y & zb.y) - __popc(xf.x & zf.x) - __popc(xf.y & zf.y);
-  const int c = (__popc(acc.z & xb.x) + __popc(acc.w & xb.y)) & 1;
+  const int c = __popc((acc.z & xb.x) ^ (acc.w & xb.y)) & 1;  // parity of z_acc . x_b
   const int v = __reduce_add_sync(0xffffffffu, 64 * t + c);
   if (lane == 0) Tp[tp0 + r] = (v >> 6) * 2 + (v & 1);
 }
@@ -656,58 +659,62 @@ blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t 
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // shared tables: entry 0 of a group is zero; entry c = entry (c with its
-  // lowest bit cleared) ^ V[first step of g + lowest bit of c]
-  for (int i = threadIdx.x; i < kSmemGroups * kCW; i += blockDim.x) {
-    const int g = i / kCW, w = i % kCW, nb = smem_group_bits(g), e0 = smem_group_base(g);
+  // shared tables, one thread per (group, quarter of its entries, word): the
+  // quarter's two top steps give its first entry, then its entries follow in
+  // Gray-code order, each one V row away from the previous (blockDim = 1024)
+  {
+    const int w = threadIdx.x & 31, sr = (threadIdx.x >> 5) & 3, g = threadIdx.x >> 7;
+    const int nb = smem_group_bits(g), e0 = smem_group_base(g) + (sr << (nb - 2));
     ulonglong2 vv[6];
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
-      const int s = 6 * g + b;
+      const int st = 6 * g + b;
       vv[b] = make_ulonglong2(0, 0);
-      if (b < nb && s < L && (uint32_t)w < nw)
-        vv[b] = make_ulonglong2(VX[(uint64_t)s * rs + u0 + w], VZ[(uint64_t)s * rs + u0 + w]);
+      if (b < nb && st < L && (uint32_t)w < nw)
+        vv[b] = make_ulonglong2(VX[(uint64_t)st * rs + u0 + w], VZ[(uint64_t)st * rs + u0 + w]);
     }
-    T[e0 * kCW + w] = make_ulonglong2(0, 0);
+    const ulonglong2 t0 = nb == 6 ? vv[4] : vv[0], t1 = nb == 6 ? vv[5] : vv[1];
+    ulonglong2 e = make_ulonglong2(((sr & 1) ? t0.x : 0) ^ ((sr & 2) ? t1.x : 0),
+                                   ((sr & 1) ? t0.y : 0) ^ ((sr & 2) ? t1.y : 0));
+    T[e0 * kCW + w] = e;
+    if (nb == 6) {
 #pragma unroll
-    for (int c = 1; c < 64; ++c) {
-      if (c >= (1 << nb)) break;
-      const int lb = (c & 1) ? 0 : (c & 2) ? 1 : (c & 4) ? 2 : (c & 8) ? 3 : (c & 16) ? 4 : 5,
-                prev = c & (c - 1);
-      const ulonglong2 pv = T[(e0 + prev) * kCW + w];
-      T[(e0 + c) * kCW + w] = make_ulonglong2(pv.x ^ vv[lb].x, pv.y ^ vv[lb].y);
+      for (int k = 1; k < 16; ++k) {
+        const int lb = (k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : 3;
+        e.x ^= vv[lb].x;
+        e.y ^= vv[lb].y;
+        T[(e0 + (k ^ (k >> 1))) * kCW + w] = e;
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tq = s_tmem + ((32u * (warp & 3)) << 16);  // lane quarter of this warp
-  if (warp < 4) {
-    // TMEM tables of this quarter: group t, entries in Gray-code order so that
-    // each differs from the previous one by one V row
-    for (int t = 0; t < 4; ++t) {
-      uint4 v[5];
+  if (warp < 16) {
+    // TMEM table t = warp / 4 of this warp's quarter, entries in Gray-code order
+    const int t = warp >> 2;
+    uint4 v[5];
 #pragma unroll
-      for (int b = 0; b < 5; ++b) {
-        const int s = kTmemStep0 + 5 * t + b;
-        v[b] = make_uint4(0, 0, 0, 0);
-        if (s < L && lane < nw) {
-          const uint2 x = reinterpret_cast<const uint2 *>(VX)[(uint64_t)s * rs + u0 + lane];
-          const uint2 z = reinterpret_cast<const uint2 *>(VZ)[(uint64_t)s * rs + u0 + lane];
-          v[b] = make_uint4(x.x, x.y, z.x, z.y);
-        }
+    for (int b = 0; b < 5; ++b) {
+      const int st = kTmemStep0 + 5 * t + b;
+      v[b] = make_uint4(0, 0, 0, 0);
+      if (st < L && lane < nw) {
+        const uint2 x = reinterpret_cast<const uint2 *>(VX)[(uint64_t)st * rs + u0 + lane];
+        const uint2 z = reinterpret_cast<const uint2 *>(VZ)[(uint64_t)st * rs + u0 + lane];
+        v[b] = make_uint4(x.x, x.y, z.x, z.y);
       }
-      uint4 e = make_uint4(0, 0, 0, 0);
-      tmem_st4(tq + 128 * t, e);
+    }
+    uint4 e = make_uint4(0, 0, 0, 0);
+    tmem_st4(tq + 128 * t, e);
 #pragma unroll
-      for (int i = 1; i < 32; ++i) {
-        const int b = __ffs(i) - 1;
-        e.x ^= v[b].x;
-        e.y ^= v[b].y;
-        e.z ^= v[b].z;
-        e.w ^= v[b].w;
-        tmem_st4(tq + 128 * t + 4 * (i ^ (i >> 1)), e);
-      }
+    for (int k = 1; k < 32; ++k) {
+      const int b = (k & 1) ? 0 : (k & 2) ? 1 : (k & 4) ? 2 : (k & 8) ? 3 : 4;
+      e.x ^= v[b].x;
+      e.y ^= v[b].y;
+      e.z ^= v[b].z;
+      e.w ^= v[b].w;
+      tmem_st4(tq + 128 * t + 4 * (k ^ (k >> 1)), e);
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
   }
@@ -717,7 +724,7 @@ blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t 
   if (L > 0) {
     const bool ok = lane < nw;
     const uint32_t word = u0 + lane;
-    const char *tl = reinterpret_cast<const char *>(T) + lane * 16;
+    const char *tb = reinterpret_cast<const char *>(T);
     const uint32_t units = gridDim.y * (blockDim.x >> 5);
     const Idx step = (Idx)units * rs;
     const uint64_t tp0 = (uint64_t)blockIdx.x * nrows;
@@ -733,15 +740,15 @@ blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t 
     for (; r < nrows; r += 3 * units, off += 3 * step) {
       apply_fetch<Idx>(a2, mn, RX, RZ, off + 2 * step, ok);
       apply_meta(mn, r + 3 * units, nrows, M, base);
-      apply_row<Idx>(a0, r, nrows, RX, RZ, off, ok, word, qubits, VX, VZ, rs, lane, tl, tq, Tp, tp0);
+      apply_row<Idx>(a0, r, nrows, RX, RZ, off, ok, word, qubits, VX, VZ, rs, lane, tb, tq, Tp, tp0);
       apply_fetch<Idx>(a0, mn, RX, RZ, off + 3 * step, ok);
       apply_meta(mn, r + 4 * units, nrows, M, base);
-      apply_row<Idx>(a1, r + units, nrows, RX, RZ, off + step, ok, word, qubits, VX, VZ, rs, lane, tl,
+      apply_row<Idx>(a1, r + units, nrows, RX, RZ, off + step, ok, word, qubits, VX, VZ, rs, lane, tb,
                         tq, Tp, tp0);
       apply_fetch<Idx>(a1, mn, RX, RZ, off + 4 * step, ok);
       apply_meta(mn, r + 5 * units, nrows, M, base);
       apply_row<Idx>(a2, r + 2 * units, nrows, RX, RZ, off + 2 * step, ok, word, qubits, VX, VZ, rs,
-                        lane, tl, tq, Tp, tp0);
+                        lane, tb, tq, Tp, tp0);
     }
   }
   tc_fence_before();

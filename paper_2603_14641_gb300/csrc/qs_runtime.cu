@@ -945,7 +945,7 @@ int qs_sim_sample(qs_sim *s, uint64_t shots, uint64_t seed, uint64_t *record, si
 }
 
 static size_t tableau_bytes(const Layout &L, int layout) {
-  if (layout == QS_LAYOUT_NATIVE) return (2ull * L.n + 1) * L.cs * 8;
+  if (layout == QS_LAYOUT_NATIVE) return (2ull * L.n + 1) * L.cw * 8;
   return (2ull * L.n * 2 * L.k + (2ull * L.n + 63) / 64) * 8;
 }
 
@@ -965,10 +965,11 @@ int qs_sim_tableau_export(qs_sim *s, int layout, void *dst, size_t dst_bytes, si
   // cudaMemcpyDefault: dst may be host or device memory
   if (layout == QS_LAYOUT_NATIVE) {
     if ((rc = ensure_cols(s))) return rc;
-    const size_t colw = (size_t)n * L.cs;
-    QS_CUDA(s, cudaMemcpyAsync(o, s->d.X, colw * 8, cudaMemcpyDefault, s->stream));
-    QS_CUDA(s, cudaMemcpyAsync(o + colw, s->d.Z, colw * 8, cudaMemcpyDefault, s->stream));
-    QS_CUDA(s, cudaMemcpyAsync(o + 2 * colw, s->d.S, (size_t)L.cs * 8, cudaMemcpyDefault, s->stream));
+    // columns of cw words out of the device's cs-word stride
+    const size_t colw = (size_t)n * L.cw, dp = (size_t)L.cw * 8, sp = (size_t)L.cs * 8;
+    QS_CUDA(s, cudaMemcpy2DAsync(o, dp, s->d.X, sp, dp, n, cudaMemcpyDefault, s->stream));
+    QS_CUDA(s, cudaMemcpy2DAsync(o + colw, dp, s->d.Z, sp, dp, n, cudaMemcpyDefault, s->stream));
+    QS_CUDA(s, cudaMemcpyAsync(o + 2 * colw, s->d.S, dp, cudaMemcpyDefault, s->stream));
     return qs_sim_sync(s);
   }
   if ((rc = ensure_rows(s))) return rc;
@@ -998,7 +999,7 @@ int qs_sim_tableau_export(qs_sim *s, int layout, void *dst, size_t dst_bytes, si
 static std::vector<std::pair<uint32_t, uint64_t>> native_padding(const Layout &L) {
   const uint64_t n = L.n, k = L.k;
   std::vector<std::pair<uint32_t, uint64_t>> pads;
-  for (uint64_t w = 0; w < L.cs; ++w) {
+  for (uint64_t w = 0; w < L.cw; ++w) {
     uint64_t pad = 0;
     for (int b = 0; b < 64; ++b) {
       const uint64_t g = 64 * w + b;
@@ -1029,17 +1030,17 @@ int qs_sim_tableau_import(qs_sim *s, int layout, const void *src, size_t src_byt
     const auto pads = native_padding(L);
     for (uint64_t c = 0; c < 2ull * n + 1; ++c)  // n X columns, n Z columns, the signs
       for (const auto &pw : pads)
-        if (in[c * L.cs + pw.first] & pw.second)
+        if (in[c * L.cw + pw.first] & pw.second)
           return fail(QS_ERR_ARG, "vector " + std::to_string(c) + " has bits outside the generators "
                                   "(word " + std::to_string(pw.first) + ")");
-    const size_t colw = (size_t)n * L.cs;
-    const size_t allw = (size_t)L.ncols * L.cs;  // padding qubit columns stay zero
+    const size_t colw = (size_t)n * L.cw, sp = (size_t)L.cw * 8, dp = (size_t)L.cs * 8;
+    const size_t allw = (size_t)L.ncols * L.cs;  // padding qubit columns and words stay zero
     QS_CUDA(s, cudaMemsetAsync(s->d.X, 0, allw * 8, s->stream));
     QS_CUDA(s, cudaMemsetAsync(s->d.Z, 0, allw * 8, s->stream));
-    QS_CUDA(s, cudaMemcpyAsync(s->d.X, in, colw * 8, cudaMemcpyHostToDevice, s->stream));
-    QS_CUDA(s, cudaMemcpyAsync(s->d.Z, in + colw, colw * 8, cudaMemcpyHostToDevice, s->stream));
-    QS_CUDA(s, cudaMemcpyAsync(s->d.S, in + 2 * colw, (size_t)L.cs * 8, cudaMemcpyHostToDevice,
-                               s->stream));
+    QS_CUDA(s, cudaMemsetAsync(s->d.S, 0, dp, s->stream));
+    QS_CUDA(s, cudaMemcpy2DAsync(s->d.X, dp, in, sp, sp, n, cudaMemcpyHostToDevice, s->stream));
+    QS_CUDA(s, cudaMemcpy2DAsync(s->d.Z, dp, in + colw, sp, sp, n, cudaMemcpyHostToDevice, s->stream));
+    QS_CUDA(s, cudaMemcpyAsync(s->d.S, in + 2 * colw, sp, cudaMemcpyHostToDevice, s->stream));
   } else {
     // bits of qubits >= n in the last word of each row must be zero
     if (n & 63) {

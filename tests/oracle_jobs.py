@@ -21,6 +21,7 @@ JOB_OF_TEST = {
     "test_oracle_parity_on_a_20k_prefix_of_the_180k_workload": "prefix_180k_20k",
     "test_oracle_parity_above_the_one_cta_symbolic_limit": "prefix_180k_30k",
     "test_10k_schedule_prefix_matches_oracle": "schedule_10k",
+    "test_oracle_parity_with_a_padded_column_stride": "prefix_180k_16200",
 }
 
 
@@ -28,8 +29,8 @@ def program(name: str):
     """The circuit of a job (layers and measurement rounds), shared by the test
     and the oracle job so both run the same program."""
     from workloads import circuits as C
-    if name in ("prefix_180k_20k", "prefix_180k_30k"):
-        n = 20_000 if name == "prefix_180k_20k" else 30_000
+    if name in ("prefix_180k_20k", "prefix_180k_30k", "prefix_180k_16200"):
+        n = {"prefix_180k_20k": 20_000, "prefix_180k_30k": 30_000, "prefix_180k_16200": 16_200}[name]
         circ = C.workload_180k_prefix(n, depth=2)
         q = np.arange(64, dtype=np.uint32)
         return C.Circuit(n=n, gates=circ.gates, layer_ptr=circ.layer_ptr,
@@ -46,7 +47,7 @@ def program(name: str):
     raise KeyError(name)
 
 
-SEEDS = {"prefix_180k_20k": 7, "prefix_180k_30k": 11, "schedule_10k": 29}
+SEEDS = {"prefix_180k_20k": 7, "prefix_180k_30k": 11, "schedule_10k": 29, "prefix_180k_16200": 13}
 
 
 def run_job(name: str) -> Dict[str, np.ndarray]:

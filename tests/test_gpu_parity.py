@@ -331,6 +331,26 @@ def test_oracle_parity_above_the_one_cta_symbolic_limit():
 
 
 @pytest.mark.slow
+def test_oracle_parity_with_a_padded_column_stride():
+    """At 16,200 qubits the column stride (2k = 508 words) is padded to 512
+    words, a 2 KB multiple, for the layout transposes; the
+    NATIVE export keeps 508-word columns. The 180,000-qubit generator's first
+    two layers and the first 64 final measurements against the oracle: record,
+    kinds and the whole tableau; the NATIVE checkpoint round-trips."""
+    sim, rec = _run_job_program("prefix_180k_16200")
+    want = _assert_against_job("prefix_180k_16200", sim, rec)
+    assert 0 < int(want["kinds"].sum()) < len(rec)
+    native, r = sim.checkpoint(qs.QS_LAYOUT_NATIVE)
+    k = (16_200 + 63) // 64
+    assert len(native) == (2 * 16_200 + 1) * ((2 * k + 3) // 4 * 4)
+    b = _sim(16_200)
+    b.restore(native, r, qs.QS_LAYOUT_NATIVE)
+    for u, v in zip(b.export(), sim.export()):
+        assert np.array_equal(u, v)
+    sim.sync()
+
+
+@pytest.mark.slow
 def test_10k_schedule_prefix_matches_oracle():
     """The 10,000-qubit workload at full size: layers 0-100 with its two
     windows of 500 mid-circuit measurements (fused gate segments, blocked
