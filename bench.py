@@ -950,6 +950,27 @@ def run_l2probe(args):
     print(json.dumps(res))
 
 
+def run_dsmemprobe(args):
+    """Evidence for the second form of fused depth at 180k qubits (one 64-row
+    word slice of every column spread over the shared memory of a 16-CTA
+    cluster, layers separated by cluster barriers): the rate of random 16-byte
+    read-modify-writes in another CTA's shared memory, against the CTA's own,
+    and the cost of a cluster barrier (probes/dsmem_probe.cu, built by
+    build.py; a probe of the memory system, not of this library's kernels)."""
+    import subprocess
+    from paper_2603_14641_gb300 import build as B
+    exe = [p for p in B.build_probes() if p.endswith("dsmem_probe")][0]
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise SystemExit(f"dsmem_probe failed: {r.stdout}{r.stderr}")
+    rows = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    print(json.dumps({"metric": "distributed shared memory: random 16-byte read-modify-write rate "
+                                "and cluster barrier cost", "unit": "TB/s", "configs": rows,
+                      "note": "a 64-row slice of the 180k tableau needs 16 CTAs (16 n bytes); a "
+                              "two-qubit gate moves 32 B of a column held by another CTA 15 times "
+                              "in 16, one layer ends at a cluster barrier"}))
+
+
 def run_reference(args):
     """The oracle as it stands on one host core, for the same metric: each step
     evolves `cpu_rows` sampled generator rows of the 180k workload's circuit
@@ -1000,7 +1021,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n180k",
-                    choices=sorted(WORKLOADS) + ["batch", "serve", "l2probe"])
+                    choices=sorted(WORKLOADS) + ["batch", "serve", "l2probe", "dsmemprobe"])
     ap.add_argument("--serve-count", type=int, default=64)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=int, default=96)
@@ -1036,6 +1057,8 @@ def main():
         run_serve(args)
     elif args.workload == "l2probe":
         run_l2probe(args)
+    elif args.workload == "dsmemprobe":
+        run_dsmemprobe(args)
     else:
         run_ours(args)
 

@@ -3,7 +3,9 @@
 Each .cu file under csrc/ is compiled in parallel with nvcc
 (-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo) and linked into
 paper_2603_14641_gb300/_lib/libqs.so (CUDA runtime linked statically). A hash
-of the sources and flags skips rebuilds when nothing changed.
+of the sources and flags skips rebuilds when nothing changed. The memory-system
+probes under probes/ (standalone programs, not part of the library) are built
+next to it.
 """
 from __future__ import annotations
 
@@ -20,6 +22,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libqs.so")
+PROBES = os.path.join(HERE, "probes")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I", INCLUDE]
@@ -81,6 +84,21 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with open(stamp, "w") as f:
         f.write(dig)
     return LIB
+
+
+def build_probes() -> list:
+    """Compiles each probes/*.cu into _lib/<name> (skipped when up to date)."""
+    os.makedirs(LIBDIR, exist_ok=True)
+    out = []
+    for src in sorted(glob.glob(os.path.join(PROBES, "*.cu"))):
+        exe = os.path.join(LIBDIR, os.path.splitext(os.path.basename(src))[0])
+        if not (os.path.exists(exe) and os.path.getmtime(exe) >= os.path.getmtime(src)):
+            cmd = [_nvcc(), *ARCH, "-O3", "-std=c++17", src, "-o", exe]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        out.append(exe)
+    return out
 
 
 if __name__ == "__main__":
