@@ -542,7 +542,22 @@ def run_full_job(args, qs, sim, circ, packed_dev, lp, shots, seed, stream, hbm, 
             "probabilistic": int((kinds == 1).sum()), "deterministic": int((kinds == 0).sum()),
             "kernels_s": {k: v[0] / 1e3 for k, v in kt.items()},
             "kernel_groups": {k: v[1] for k, v in kt.items()},
-            "apply_pass": apply_roofline(kt, circ.n, hbm, peak_kind)}
+            "apply_pass": _job_apply(apply_roofline(kt, circ.n, hbm, peak_kind))}
+
+
+def _job_apply(a):
+    """Over the whole final measurement the blocks leave a growing share of the
+    rows alone (the +-Z_q pivots of earlier blocks are neither read nor
+    written), so the full-tableau byte count overstates what later blocks move:
+    the job's figures are kept, under names that say so; the roofline fraction
+    of the apply pass is the one of `phases.measurement` (dense blocks)."""
+    if not a:
+        return a
+    return {"kernel": a["kernel"], "launches": a["launches"], "ms_per_launch": a["ms_per_launch"],
+            "full_tableau_bytes_per_launch": a["algorithmic_bytes_per_launch"],
+            "full_tableau_equivalent_gbs": a["achieved_gbs"],
+            "note": "average over all blocks; later blocks skip the rows they leave alone, so "
+                    "this is not a roofline fraction", "timing": a["timing"]}
 
 
 def noisy_sampling(args, qs, sim, circ, prog, packed_dev, lp, qdev, shots, seed, stream, rec_dev, M,
