@@ -1036,7 +1036,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n180k",
-                    choices=sorted(WORKLOADS) + ["batch", "serve", "l2probe", "dsmemprobe"])
+                    choices=sorted(WORKLOADS) + ["batch", "serve", "l2probe", "dsmemprobe",
+                                                 "inverse"])
     ap.add_argument("--serve-count", type=int, default=64)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=int, default=96)
@@ -1074,6 +1075,9 @@ def main():
         run_l2probe(args)
     elif args.workload == "dsmemprobe":
         run_dsmemprobe(args)
+    elif args.workload == "inverse":
+        print(json.dumps({"metric": "inverse-tableau mode (Alg. 1) vs CHP on the 10,000-qubit "
+                                    "workload", **inverse_mode_summary()}))
     else:
         run_ours(args)
 

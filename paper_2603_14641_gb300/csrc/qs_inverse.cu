@@ -44,6 +44,8 @@
 //     outcome is S_S[q] (nothing changes). Record, kind, pivot reset.
 #include <climits>
 
+#include <algorithm>
+
 #include "qs_internal.cuh"
 
 namespace qs {
@@ -257,46 +259,90 @@ inv_targets_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_
   uint32_t i0 = c * rows_per_chunk;
   const uint32_t i1 = min(n, i0 + rows_per_chunk);
   if (i0 <= p) i0 = p + 1;  // targets come after the pivot
-  for (uint32_t i = i0; i < i1; ++i) {
-    const uint64_t r = lo + i;
-    if (((__ldg(colx + (r >> 5)) >> (r & 31)) & 1u) == 0) continue;
-    const uint64_t xs = RX[r * rs + u], zs = RZ[r * rs + u];
-    const uint64_t xd = RX[(uint64_t)i * rs + u], zd = RZ[(uint64_t)i * rs + u];
-    RX[r * rs + u] = xs ^ xsp;  // S_t <- S_t S_p (bits)
-    RZ[r * rs + u] = zs ^ zsp;
+  // the next target at or after row i (stabilizer rows with XS[t][q] = 1)
+  auto next = [&](uint32_t i) {
+    for (; i < i1; ++i) {
+      const uint64_t r = lo + i;
+      if ((__ldg(colx + (r >> 5)) >> (r & 31)) & 1u) break;
+    }
+    return i;
+  };
+  // the words of the next target are loaded before the current one is
+  // stored (distinct rows), so each target costs one memory latency less
+  uint32_t t = next(i0);
+  uint64_t xs = 0, zs = 0, xd = 0, zd = 0;
+  if (t < i1) {
+    xs = RX[(lo + t) * rs + u]; zs = RZ[(lo + t) * rs + u];
+    xd = RX[(uint64_t)t * rs + u]; zd = RZ[(uint64_t)t * rs + u];
+  }
+  while (t < i1) {
+    const uint32_t t2 = next(t + 1);
+    uint64_t nxs = 0, nzs = 0, nxd = 0, nzd = 0;
+    if (t2 < i1) {
+      nxs = RX[(lo + t2) * rs + u]; nzs = RZ[(lo + t2) * rs + u];
+      nxd = RX[(uint64_t)t2 * rs + u]; nzd = RZ[(uint64_t)t2 * rs + u];
+    }
+    RX[(lo + t) * rs + u] = xs ^ xsp;  // S_t <- S_t S_p (bits)
+    RZ[(lo + t) * rs + u] = zs ^ zsp;
     fx ^= xsp & xd & ~(xd0 ^ xs);
     fz ^= zsp & zd & ~(zd0 ^ zs);
     lx ^= xd & dx;  // dx so far: XOR of the chunk's earlier targets
     lz ^= zd & dz;
     dx ^= xd;
     dz ^= zd;
+    xs = nxs; zs = nzs; xd = nxd; zd = nzd;
+    t = t2;
   }
   uint64_t *o = part + (size_t)6 * c * rs + u;
   o[0] = dx; o[rs] = dz; o[2 * (size_t)rs] = fx; o[3 * (size_t)rs] = fz; o[4 * (size_t)rs] = lx;
   o[5 * (size_t)rs] = lz;
 }
 
+// Chunk partials merge in index order: (D, L, F) of an earlier range followed
+// by (D', L', F') of a later one is (D ^ D', L ^ L' ^ (D & D'), F ^ F'), the
+// pairs across the two ranges being D & D'. A block covers 32 words (lane =
+// word, coalesced rows of the partials); warp w merges chunks 32 w .. 32 w + 31
+// in order, then warp 0 merges the 8 warps' results in order.
 __global__ void __launch_bounds__(256)
 inv_combine_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint64_t *__restrict__ qsig,
                    uint32_t rs, uint32_t k, const int64_t *__restrict__ mst,
                    const uint64_t *__restrict__ part, uint32_t chunks) {
+  __shared__ uint64_t red[6][8][32];
   const int64_t pp = mst[kMsPivot];
   if (pp == kInvNoPivot) return;
-  const uint32_t u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= rs) return;
-  const uint64_t lo = 64ull * k;
-  const uint64_t p = (uint64_t)(pp - (int64_t)lo);
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t u = blockIdx.x * 32 + lane;
   uint64_t px = 0, pz = 0, fx = 0, fz = 0, lx = 0, lz = 0;
-  for (uint32_t c = 0; c < chunks; ++c) {
-    const uint64_t *o = part + (size_t)6 * c * rs + u;
-    const uint64_t dx = o[0], dz = o[rs];
-    fx ^= o[2 * (size_t)rs];
-    fz ^= o[3 * (size_t)rs];
-    lx ^= o[4 * (size_t)rs] ^ (px & dx);  // pairs across chunks: earlier chunks' XOR with this one
-    lz ^= o[5 * (size_t)rs] ^ (pz & dz);
+  if (u < rs) {
+    const uint32_t c1 = min(chunks, 32 * (warp + 1));
+#pragma unroll 4
+    for (uint32_t c = 32 * warp; c < c1; ++c) {
+      const uint64_t *o = part + (size_t)6 * c * rs + u;
+      const uint64_t dx = o[0], dz = o[rs];
+      fx ^= o[2 * (size_t)rs];
+      fz ^= o[3 * (size_t)rs];
+      lx ^= o[4 * (size_t)rs] ^ (px & dx);
+      lz ^= o[5 * (size_t)rs] ^ (pz & dz);
+      px ^= dx;
+      pz ^= dz;
+    }
+  }
+  red[0][warp][lane] = px; red[1][warp][lane] = pz; red[2][warp][lane] = fx;
+  red[3][warp][lane] = fz; red[4][warp][lane] = lx; red[5][warp][lane] = lz;
+  __syncthreads();
+  if (warp != 0 || u >= rs) return;
+  px = pz = fx = fz = lx = lz = 0;
+  for (uint32_t w = 0; w < 8; ++w) {
+    const uint64_t dx = red[0][w][lane], dz = red[1][w][lane];
+    fx ^= red[2][w][lane];
+    fz ^= red[3][w][lane];
+    lx ^= red[4][w][lane] ^ (px & dx);
+    lz ^= red[5][w][lane] ^ (pz & dz);
     px ^= dx;
     pz ^= dz;
   }
+  const uint64_t lo = 64ull * k;
+  const uint64_t p = (uint64_t)(pp - (int64_t)lo);
   const uint64_t xsp = RX[(lo + p) * rs + u], zsp = RZ[(lo + p) * rs + u];
   RX[p * rs + u] ^= px;  // D_p <- D_p prod_t D_t (bits)
   RZ[p * rs + u] ^= pz;
@@ -365,10 +411,11 @@ cudaError_t launch_inv_measure_one(const Dev &d, const uint32_t *qubits, uint32_
   launch_gather(d, qubits, i, s);
   const uint32_t rows_per_chunk = (L.n + kInvChunks - 1) / kInvChunks;
   const uint32_t chunks = (L.n + rows_per_chunk - 1) / rows_per_chunk;
-  inv_targets_kernel<<<dim3(chunks, (L.rs + 255) / 256), 256, 0, s>>>(d.RX, d.RZ, L.rs, L.n, L.k, d.colx,
+  const uint32_t tt = std::min<uint32_t>(256, (L.rs + 31) / 32 * 32);  // no idle warps when rs < 256
+  inv_targets_kernel<<<dim3(chunks, (L.rs + tt - 1) / tt), tt, 0, s>>>(d.RX, d.RZ, L.rs, L.n, L.k, d.colx,
                                                                       d.mst, d.inv_part, rows_per_chunk);
-  inv_combine_kernel<<<(L.rs + 255) / 256, 256, 0, s>>>(d.RX, d.RZ, d.qsig, L.rs, L.k, d.mst, d.inv_part,
-                                                       chunks);
+  inv_combine_kernel<<<(L.rs + 31) / 32, 256, 0, s>>>(d.RX, d.RZ, d.qsig, L.rs, L.k, d.mst, d.inv_part,
+                                                     chunks);
   inv_finalize_kernel<<<1, 1024, 0, s>>>(d.RX, d.RZ, d.qsig, L.rs, L.n, L.k, qubits, i, d.mst, midx,
                                          key.seed, key.shot, d.record, d.kinds);
   if (launches) *launches += 4;
