@@ -43,7 +43,7 @@ constexpr int kCW = 32;               // column words per phase-3 chunk
 struct BlkState {
   int64_t slot[3];     // pivot search results, rotating
   int32_t len;         // steps completed in this block
-  int32_t pad;
+  uint32_t ntouched;   // rows the block changes (entries of the apply pass's row list)
   int64_t piv[64];     // pivot row of each step
   uint64_t mpiv[64];   // steps that targeted the pivot row before it became pivot
   int32_t A[64];       // |x_V & z_V| mod 4 (summed over words)
@@ -62,7 +62,7 @@ __device__ __forceinline__ int m4(int v) { return ((v % 4) + 4) % 4; }
 __global__ void blk_reset_kernel(BlkState *st, int B, uint32_t nwin) {
   const int t = threadIdx.x;
   if (t < 3) st->slot[t] = kBlkNone;
-  if (t == 0) { st->len = B; st->err = 0; }
+  if (t == 0) { st->len = B; st->err = 0; st->ntouched = 0; }
   if (t < 64) {
     st->piv[t] = kBlkNone; st->mpiv[t] = 0; st->A[t] = 0; st->B0[t] = 0; st->Cp[t] = 0;
     st->rV[t] = 0; st->G[t] = 0;
@@ -474,27 +474,58 @@ __global__ void __launch_bounds__(64) blk_signs_kernel(const uint64_t *__restric
 constexpr int kEntryBytes = kCW * 16;   // 512
 
 struct ApplyRow {
+  uint32_t r;
   int32_t b;
   uint32_t lo, hi;  // M_r
   uint2 x, z;       // this lane's word of x and z, as 32-bit halves
 };
 
-// pattern M_r and base_r of a row (one stage ahead of its words)
+// row, pattern M_r and base_r of a row the block changes (one stage ahead of
+// its words): entry j of the row list, or row = nrows past its end
 struct ApplyMeta {
+  uint32_t r;
   int32_t b;
   uint32_t lo, hi;
 };
 
-__device__ __forceinline__ void apply_meta(ApplyMeta &m, uint32_t r, uint32_t nrows, const uint64_t *M,
-                                           const int32_t *base) {
+__device__ __forceinline__ void apply_meta(ApplyMeta &m, uint32_t j, uint32_t cnt, uint32_t nrows,
+                                           const uint4 *list) {
+  m.r = nrows;
   m.b = kBaseOrig;
   m.lo = m.hi = 0;
-  if (r < nrows) {
-    m.b = __ldg(base + r);
-    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(M) + r);
-    m.lo = v.x;
-    m.hi = v.y;
+  if (j < cnt) {
+    const uint4 e = __ldg(list + j);
+    m.r = e.x;
+    m.b = (int32_t)e.y;
+    m.lo = e.z;
+    m.hi = e.w;
   }
+}
+
+// the row list: every row the block changes (a step targeted it, or its base
+// changed: replaced destabilizers and the new pivots) with its pattern and
+// base, in groups of consecutive rows (one atomic per warp). Rows left alone
+// (M_r = 0, original base: e.g. the +-Z_q pivot rows of earlier blocks) are
+// neither listed, read nor written.
+__global__ void __launch_bounds__(256)
+blk_list_kernel(uint64_t nrows, const uint64_t *__restrict__ M, const int32_t *__restrict__ base,
+                uint4 *__restrict__ list, BlkState *st) {
+  const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t m = 0;
+  int32_t b = kBaseOrig;
+  if (r < nrows) {
+    m = M[r];
+    b = base[r];
+  }
+  const bool touched = r < nrows && (b != kBaseOrig || m != 0);
+  const uint32_t ball = __ballot_sync(0xffffffffu, touched);
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t at = 0;
+  if (lane == 0 && ball) at = atomicAdd(&st->ntouched, (uint32_t)__popc(ball));
+  at = __shfl_sync(0xffffffffu, at, 0);
+  if (touched)
+    list[at + __popc(ball & ((1u << lane) - 1))] =
+        make_uint4((uint32_t)r, (uint32_t)b, (uint32_t)m, (uint32_t)(m >> 32));
 }
 
 // the row's words, fetched only when the row changes: a row that no step
@@ -502,12 +533,15 @@ __device__ __forceinline__ void apply_meta(ApplyMeta &m, uint32_t r, uint32_t nr
 // the +-Z_q pivot rows of earlier blocks) is neither read nor written
 template <typename Idx>
 __device__ __forceinline__ void apply_fetch(ApplyRow &a, const ApplyMeta &m, const uint64_t *RX,
-                                            const uint64_t *RZ, Idx off, bool ok) {
+                                            const uint64_t *RZ, uint32_t rs, uint32_t word, uint32_t nrows,
+                                            bool ok) {
+  a.r = m.r;
   a.b = m.b;
   a.lo = m.lo;
   a.hi = m.hi;
   a.x = a.z = make_uint2(0, 0);
-  if (ok && (m.b != kBaseOrig || (m.lo | m.hi) != 0)) {
+  if (ok && m.r < nrows) {
+    const Idx off = (Idx)m.r * rs + word;
     a.x = reinterpret_cast<const uint2 *>(RX)[off];
     a.z = reinterpret_cast<const uint2 *>(RZ)[off];
   }
@@ -587,12 +621,14 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 template <typename Idx>
-__device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t r, uint32_t nrows, uint64_t *RX,
-                                             uint64_t *RZ, Idx off, bool ok, uint32_t word,
+__device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t nrows, uint64_t *RX,
+                                             uint64_t *RZ, bool ok, uint32_t word,
                                              const uint32_t *qubits, const uint64_t *VX,
                                              const uint64_t *VZ, uint32_t rs, uint32_t lane,
                                              const char *tb, uint32_t tq, int32_t *Tp, uint64_t tp0) {
+  const uint32_t r = a.r;
   if (r >= nrows) return;  // uniform over the warp
+  const Idx off = (Idx)r * rs + word;
   uint2 *px = reinterpret_cast<uint2 *>(RX), *pz = reinterpret_cast<uint2 *>(RZ);
   if (a.b >= kBasePivot) {  // pivot row of step j: +-Z_q (sign set by blk_rows_kernel)
     const uint32_t q = qubits[a.b - kBasePivot];
@@ -644,8 +680,8 @@ template <typename Idx>
 __global__ void __launch_bounds__(1024, 1)
 blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t rs, uint32_t nrows,
                     const uint32_t *__restrict__ qubits, const uint64_t *__restrict__ VX,
-                    const uint64_t *__restrict__ VZ, const uint64_t *__restrict__ M,
-                    const int32_t *__restrict__ base, int32_t *__restrict__ Tp, const BlkState *st) {
+                    const uint64_t *__restrict__ VZ, const uint4 *__restrict__ list,
+                    int32_t *__restrict__ Tp, const BlkState *st) {
   extern __shared__ ulonglong2 T[];  // [kSmemEntries][kCW] of (x word, z word)
   __shared__ uint32_t s_tmem;
   const int L = st->len;
@@ -721,34 +757,32 @@ blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  const uint32_t cnt = st->ntouched;
   if (L > 0) {
     const bool ok = lane < nw;
     const uint32_t word = u0 + lane;
     const char *tb = reinterpret_cast<const char *>(T);
     const uint32_t units = gridDim.y * (blockDim.x >> 5);
-    const Idx step = (Idx)units * rs;
     const uint64_t tp0 = (uint64_t)blockIdx.x * nrows;
-    uint32_t r = blockIdx.y * (blockDim.x >> 5) + warp;
-    Idx off = (Idx)r * rs + word;
+    // the warp's entries of the row list: j, j + units, ...
+    uint32_t j = blockIdx.y * (blockDim.x >> 5) + warp;
     ApplyRow a0, a1, a2;
     ApplyMeta mn;
-    apply_meta(mn, r, nrows, M, base);
-    apply_fetch<Idx>(a0, mn, RX, RZ, off, ok);
-    apply_meta(mn, r + units, nrows, M, base);
-    apply_fetch<Idx>(a1, mn, RX, RZ, off + step, ok);
-    apply_meta(mn, r + 2 * units, nrows, M, base);
-    for (; r < nrows; r += 3 * units, off += 3 * step) {
-      apply_fetch<Idx>(a2, mn, RX, RZ, off + 2 * step, ok);
-      apply_meta(mn, r + 3 * units, nrows, M, base);
-      apply_row<Idx>(a0, r, nrows, RX, RZ, off, ok, word, qubits, VX, VZ, rs, lane, tb, tq, Tp, tp0);
-      apply_fetch<Idx>(a0, mn, RX, RZ, off + 3 * step, ok);
-      apply_meta(mn, r + 4 * units, nrows, M, base);
-      apply_row<Idx>(a1, r + units, nrows, RX, RZ, off + step, ok, word, qubits, VX, VZ, rs, lane, tb,
-                        tq, Tp, tp0);
-      apply_fetch<Idx>(a1, mn, RX, RZ, off + 4 * step, ok);
-      apply_meta(mn, r + 5 * units, nrows, M, base);
-      apply_row<Idx>(a2, r + 2 * units, nrows, RX, RZ, off + 2 * step, ok, word, qubits, VX, VZ, rs,
-                        lane, tb, tq, Tp, tp0);
+    apply_meta(mn, j, cnt, nrows, list);
+    apply_fetch<Idx>(a0, mn, RX, RZ, rs, word, nrows, ok);
+    apply_meta(mn, j + units, cnt, nrows, list);
+    apply_fetch<Idx>(a1, mn, RX, RZ, rs, word, nrows, ok);
+    apply_meta(mn, j + 2 * units, cnt, nrows, list);
+    for (; j < cnt; j += 3 * units) {
+      apply_fetch<Idx>(a2, mn, RX, RZ, rs, word, nrows, ok);
+      apply_meta(mn, j + 3 * units, cnt, nrows, list);
+      apply_row<Idx>(a0, nrows, RX, RZ, ok, word, qubits, VX, VZ, rs, lane, tb, tq, Tp, tp0);
+      apply_fetch<Idx>(a0, mn, RX, RZ, rs, word, nrows, ok);
+      apply_meta(mn, j + 4 * units, cnt, nrows, list);
+      apply_row<Idx>(a1, nrows, RX, RZ, ok, word, qubits, VX, VZ, rs, lane, tb, tq, Tp, tp0);
+      apply_fetch<Idx>(a1, mn, RX, RZ, rs, word, nrows, ok);
+      apply_meta(mn, j + 5 * units, cnt, nrows, list);
+      apply_row<Idx>(a2, nrows, RX, RZ, ok, word, qubits, VX, VZ, rs, lane, tb, tq, Tp, tp0);
     }
   }
   tc_fence_before();
@@ -817,7 +851,7 @@ static uint32_t blk_chunks(const Layout &L) { return (L.rs + kCW - 1) / kCW; }
 size_t blocked_scratch_bytes(const Layout &L) {
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   return 3 * al(L.nrows * 8) + al(L.nrows * 4) + al((size_t)blk_chunks(L) * L.nrows * 4) +
-         2 * al(64ull * L.rs * 8) + al(sizeof(BlkState));
+         2 * al(64ull * L.rs * 8) + al(sizeof(BlkState)) + al(L.nrows * 16);
 }
 
 static std::atomic<uint64_t> g_apply_attr_set{0};
@@ -839,6 +873,7 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   uint64_t *VX = reinterpret_cast<uint64_t *>(take(64ull * L.rs * 8));
   uint64_t *VZ = reinterpret_cast<uint64_t *>(take(64ull * L.rs * 8));
   BlkState *st = reinterpret_cast<BlkState *>(take(sizeof(BlkState)));
+  uint4 *list = reinterpret_cast<uint4 *>(take(L.nrows * 16));
   const unsigned rb = (unsigned)((L.nrows + 255) / 256);
   const size_t smem = (size_t)kSmemEntries * kEntryBytes;
   cudaError_t ea = once_per_device(g_apply_attr_set, [&]() {
@@ -873,6 +908,7 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   blk_vrows_kernel<<<dim3(chunks, kVrowSplit), kVrowThreads, kVrowSmem, s>>>(d.RX, d.RZ, L.rs, VX,
                                                                               VZ, st);
   blk_signs_kernel<<<1, 64, 0, s>>>(d.S, st, d.err);
+  blk_list_kernel<<<rb, 256, 0, s>>>(L.nrows, M, base, list, st);
   tend(d.timer, QS_TIME_BLK_PIVOT_ROWS, s);
   // about 8 waves of one block per SM (the tables take 226 KB of shared
   // memory and all of TMEM), but at least 512 rows per block so that building
@@ -882,16 +918,16 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   tbegin(d.timer, QS_TIME_BLK_APPLY, s);
   if (!d.wide_offsets && (uint64_t)L.nrows * L.rs < (1ull << 32))
     blk_apply_kernel<uint32_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
-        d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, M, base, Tp, st);
+        d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, list, Tp, st);
   else
     blk_apply_kernel<uint64_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
-        d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, M, base, Tp, st);
+        d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, list, Tp, st);
   tend(d.timer, QS_TIME_BLK_APPLY, s);
   tbegin(d.timer, QS_TIME_BLK_SIGNS, s);
   blk_rows_kernel<<<rb, 256, 0, s>>>(d.S, L.nrows, qubits, M, base, Tp, chunks, st, m0, key.seed,
                                      key.shot, d.record, d.kinds, d.err);
   tend(d.timer, QS_TIME_BLK_SIGNS, s);
-  if (launches) *launches += 6 + sym_launches;
+  if (launches) *launches += 7 + sym_launches;
   if (len_dev) *len_dev = &st->len;
   return cudaGetLastError();
 }
