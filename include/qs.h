@@ -519,7 +519,8 @@ uint64_t qs_sim_launch_count(const qs_sim *sim);
 /* Kernel classes of qs_sim_timing (the phases of Alg. 2 and of the blocked
  * measurement): gate layers (Sec. 4.4), the layout switch between column- and
  * row-major (Sec. 4.5), the blocked measurement's symbolic pass, its pivot
- * rows and their signs, its apply pass over the row-major tableau and its
+ * rows with their signs and the list of rows the block changes, its apply
+ * pass over the row-major tableau and its
  * per-row signs and record, measurements outside blocks (single and
  * pipelined), and frame sampling (Sec. 5). */
 enum {
