@@ -242,45 +242,45 @@ cudaError_t launch_inv_gate_layer(const Dev &d, const uint32_t *packed, uint32_t
 // measurement
 // ---------------------------------------------------------------------------
 // partials of chunk c: part[(6 c + j) * rs + u], j = 0 Dx, 1 Dz, 2 Fx, 3 Fz, 4 Lx, 5 Lz
-__global__ void __launch_bounds__(256)
-inv_targets_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t rs, uint32_t n,
-                   uint32_t k, const uint32_t *__restrict__ colx, const int64_t *__restrict__ mst,
-                   uint64_t *__restrict__ part, uint32_t rows_per_chunk) {
-  const int64_t pp = mst[kMsPivot];
-  if (pp == kInvNoPivot) return;
+
+// one (row chunk c, word u) of the target pass; pp = pivot (packed row)
+__device__ __forceinline__ void inv_targets_item(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ,
+                                                 uint32_t rs, uint32_t n, uint32_t k,
+                                                 const uint32_t *__restrict__ colx, int64_t pp,
+                                                 uint64_t *__restrict__ part, uint32_t rows_per_chunk,
+                                                 uint32_t c, uint32_t u) {
   const uint64_t lo = 64ull * k;
   const uint32_t p = (uint32_t)(pp - (int64_t)lo);
-  const uint32_t c = blockIdx.x;
-  const uint32_t u = blockIdx.y * blockDim.x + threadIdx.x;
-  if (u >= rs) return;
-  const uint64_t xsp = RX[(lo + p) * rs + u], zsp = RZ[(lo + p) * rs + u];
-  const uint64_t xd0 = RX[(uint64_t)p * rs + u], zd0 = RZ[(uint64_t)p * rs + u];
+  const uint64_t xsp = *(RX + (lo + p) * rs + u), zsp = *(RZ + (lo + p) * rs + u);
+  const uint64_t xd0 = *(RX + (uint64_t)p * rs + u), zd0 = *(RZ + (uint64_t)p * rs + u);
   uint64_t dx = 0, dz = 0, fx = 0, fz = 0, lx = 0, lz = 0;
   uint32_t i0 = c * rows_per_chunk;
   const uint32_t i1 = min(n, i0 + rows_per_chunk);
   if (i0 <= p) i0 = p + 1;  // targets come after the pivot
   // the next target at or after row i (stabilizer rows with XS[t][q] = 1)
   auto next = [&](uint32_t i) {
-    for (; i < i1; ++i) {
+    while (i < i1) {  // a word of column bits at a time
       const uint64_t r = lo + i;
-      if ((__ldg(colx + (r >> 5)) >> (r & 31)) & 1u) break;
+      const uint32_t m = *(colx + (r >> 5)) >> (r & 31);
+      if (m) return min(i1, i + (uint32_t)__ffs(m) - 1);
+      i += 32 - (uint32_t)(r & 31);
     }
-    return i;
+    return i1;
   };
   // the words of the next target are loaded before the current one is
   // stored (distinct rows), so each target costs one memory latency less
   uint32_t t = next(i0);
   uint64_t xs = 0, zs = 0, xd = 0, zd = 0;
   if (t < i1) {
-    xs = RX[(lo + t) * rs + u]; zs = RZ[(lo + t) * rs + u];
-    xd = RX[(uint64_t)t * rs + u]; zd = RZ[(uint64_t)t * rs + u];
+    xs = *(RX + (lo + t) * rs + u); zs = *(RZ + (lo + t) * rs + u);
+    xd = *(RX + (uint64_t)t * rs + u); zd = *(RZ + (uint64_t)t * rs + u);
   }
   while (t < i1) {
     const uint32_t t2 = next(t + 1);
     uint64_t nxs = 0, nzs = 0, nxd = 0, nzd = 0;
     if (t2 < i1) {
-      nxs = RX[(lo + t2) * rs + u]; nzs = RZ[(lo + t2) * rs + u];
-      nxd = RX[(uint64_t)t2 * rs + u]; nzd = RZ[(uint64_t)t2 * rs + u];
+      nxs = *(RX + (lo + t2) * rs + u); nzs = *(RZ + (lo + t2) * rs + u);
+      nxd = *(RX + (uint64_t)t2 * rs + u); nzd = *(RZ + (uint64_t)t2 * rs + u);
     }
     RX[(lo + t) * rs + u] = xs ^ xsp;  // S_t <- S_t S_p (bits)
     RZ[(lo + t) * rs + u] = zs ^ zsp;
@@ -300,29 +300,27 @@ inv_targets_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_
 
 // Chunk partials merge in index order: (D, L, F) of an earlier range followed
 // by (D', L', F') of a later one is (D ^ D', L ^ L' ^ (D & D'), F ^ F'), the
-// pairs across the two ranges being D & D'. A block covers 32 words (lane =
-// word, coalesced rows of the partials); warp w merges chunks 32 w .. 32 w + 31
-// in order, then warp 0 merges the 8 warps' results in order.
-__global__ void __launch_bounds__(256)
-inv_combine_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint64_t *__restrict__ qsig,
-                   uint32_t rs, uint32_t k, const int64_t *__restrict__ mst,
-                   const uint64_t *__restrict__ part, uint32_t chunks) {
-  __shared__ uint64_t red[6][8][32];
-  const int64_t pp = mst[kMsPivot];
-  if (pp == kInvNoPivot) return;
+// pairs across the two ranges being D & D'. A block of 8 warps covers 32
+// words (lane = word, coalesced rows of the partials): warp w merges chunks
+// 32 w .. 32 w + 31 in order, then warp 0 merges the 8 warps' results in
+// order. Called by every thread of the block (it holds a block barrier).
+__device__ __forceinline__ void inv_combine_group(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ,
+                                                  uint64_t *__restrict__ qsig, uint32_t rs, uint32_t k,
+                                                  int64_t pp, const uint64_t *__restrict__ part,
+                                                  uint32_t chunks, uint32_t group, uint64_t (*red)[8][32]) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t u = blockIdx.x * 32 + lane;
+  const uint32_t u = group * 32 + lane;
   uint64_t px = 0, pz = 0, fx = 0, fz = 0, lx = 0, lz = 0;
   if (u < rs) {
     const uint32_t c1 = min(chunks, 32 * (warp + 1));
 #pragma unroll 4
     for (uint32_t c = 32 * warp; c < c1; ++c) {
       const uint64_t *o = part + (size_t)6 * c * rs + u;
-      const uint64_t dx = o[0], dz = o[rs];
-      fx ^= o[2 * (size_t)rs];
-      fz ^= o[3 * (size_t)rs];
-      lx ^= o[4 * (size_t)rs] ^ (px & dx);
-      lz ^= o[5 * (size_t)rs] ^ (pz & dz);
+      const uint64_t dx = *(o), dz = *(o + rs);
+      fx ^= *(o + 2 * (size_t)rs);
+      fz ^= *(o + 3 * (size_t)rs);
+      lx ^= *(o + 4 * (size_t)rs) ^ (px & dx);
+      lz ^= *(o + 5 * (size_t)rs) ^ (pz & dz);
       px ^= dx;
       pz ^= dz;
     }
@@ -330,24 +328,105 @@ inv_combine_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint64_
   red[0][warp][lane] = px; red[1][warp][lane] = pz; red[2][warp][lane] = fx;
   red[3][warp][lane] = fz; red[4][warp][lane] = lx; red[5][warp][lane] = lz;
   __syncthreads();
-  if (warp != 0 || u >= rs) return;
-  px = pz = fx = fz = lx = lz = 0;
-  for (uint32_t w = 0; w < 8; ++w) {
-    const uint64_t dx = red[0][w][lane], dz = red[1][w][lane];
-    fx ^= red[2][w][lane];
-    fz ^= red[3][w][lane];
-    lx ^= red[4][w][lane] ^ (px & dx);
-    lz ^= red[5][w][lane] ^ (pz & dz);
-    px ^= dx;
-    pz ^= dz;
+  if (warp == 0 && u < rs) {
+    px = pz = fx = fz = lx = lz = 0;
+    for (uint32_t w = 0; w < 8; ++w) {
+      const uint64_t dx = red[0][w][lane], dz = red[1][w][lane];
+      fx ^= red[2][w][lane];
+      fz ^= red[3][w][lane];
+      lx ^= red[4][w][lane] ^ (px & dx);
+      lz ^= red[5][w][lane] ^ (pz & dz);
+      px ^= dx;
+      pz ^= dz;
+    }
+    const uint64_t lo = 64ull * k;
+    const uint64_t p = (uint64_t)(pp - (int64_t)lo);
+    const uint64_t xsp = *(RX + (lo + p) * rs + u), zsp = *(RZ + (lo + p) * rs + u);
+    RX[p * rs + u] = *(RX + p * rs + u) ^ px;  // D_p <- D_p prod_t D_t (bits)
+    RZ[p * rs + u] = *(RZ + p * rs + u) ^ pz;
+    qsig[u] = *(qsig + u) ^ fx ^ (xsp & lx);
+    qsig[rs + u] = *(qsig + rs + u) ^ fz ^ (zsp & lz);
+  }
+  __syncthreads();  // red is reused by the block's next group
+}
+
+// One block: the H or H_YZ injection on the pivot, then the X injection when
+// S_S[q] differs from the keyed coin; the outcome is the coin. A
+// deterministic outcome is S_S[q] (nothing changes). Record, kind, pivot
+// reset. Called by every thread of the block.
+__device__ __forceinline__ void inv_finalize_block(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ,
+                                                   uint64_t *__restrict__ qsig, uint32_t rs, uint32_t k,
+                                                   uint32_t q, int64_t pp, int64_t *__restrict__ mst,
+                                                   uint64_t midx, uint64_t seed, uint64_t shot,
+                                                   uint8_t *__restrict__ record, uint8_t *__restrict__ kinds) {
+  const uint32_t tid = threadIdx.x;
+  if (pp == kInvNoPivot) {  // deterministic: the outcome is S_S[q]
+    if (tid == 0) {
+      record[midx] = (uint8_t)((*(qsig + (q >> 6)) >> (q & 63)) & 1u);
+      kinds[midx] = 0;
+    }
+    return;
   }
   const uint64_t lo = 64ull * k;
   const uint64_t p = (uint64_t)(pp - (int64_t)lo);
-  const uint64_t xsp = RX[(lo + p) * rs + u], zsp = RZ[(lo + p) * rs + u];
-  RX[p * rs + u] ^= px;  // D_p <- D_p prod_t D_t (bits)
-  RZ[p * rs + u] ^= pz;
-  qsig[u] ^= fx ^ (xsp & lx);
-  qsig[rs + u] ^= fz ^ (zsp & lz);
+  uint64_t *xs = RX + (lo + p) * rs, *xd = RX + p * rs, *zs = RZ + (lo + p) * rs, *zd = RZ + p * rs;
+  // Y case (the pivot's destabilizer has z at q in the Z_q image): H_YZ, else H
+  const bool yz = ((*(xd + (q >> 6)) >> (q & 63)) & 1u) != 0;
+  __syncthreads();  // every thread has read xd[q >> 6] before it changes
+  for (uint32_t u = tid; u < rs; u += blockDim.x) {
+    uint64_t a = *(xs + u), b = *(xd + u), c = *(zs + u), e = *(zd + u);
+    uint64_t s0 = *(qsig + u), s1 = *(qsig + rs + u);
+    if (yz) {
+      s0 ^= a & ~b;
+      a ^= b;
+      s1 ^= c & ~e;
+      c ^= e;
+    } else {
+      s0 ^= a & b;
+      uint64_t t = a; a = b; b = t;
+      s1 ^= c & e;
+      t = c; c = e; e = t;
+    }
+    xs[u] = a; xd[u] = b; zs[u] = c; zd[u] = e;
+    qsig[u] = s0;
+    qsig[rs + u] = s1;
+  }
+  __syncthreads();
+  const uint32_t coin = (uint32_t)(philox4x64_10(midx, shot, 0, 0, seed, kCoinKey).v[0] & 1u);
+  const uint32_t sq = (uint32_t)((*(qsig + (q >> 6)) >> (q & 63)) & 1u);
+  __syncthreads();  // every thread has read S_S[q] before the X injection changes it
+  if (sq != coin)
+    for (uint32_t u = tid; u < rs; u += blockDim.x) {
+      qsig[u] = *(qsig + u) ^ *(xd + u);
+      qsig[rs + u] = *(qsig + rs + u) ^ *(zd + u);
+    }
+  if (tid == 0) {
+    record[midx] = (uint8_t)coin;
+    kinds[midx] = 1;
+    mst[kMsPivot] = kInvNoPivot;
+  }
+}
+
+// standalone kernels (one launch per phase; the gather is the CHP path's)
+__global__ void __launch_bounds__(256)
+inv_targets_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t rs, uint32_t n,
+                   uint32_t k, const uint32_t *__restrict__ colx, const int64_t *__restrict__ mst,
+                   uint64_t *__restrict__ part, uint32_t rows_per_chunk) {
+  const int64_t pp = mst[kMsPivot];
+  if (pp == kInvNoPivot) return;
+  const uint32_t u = blockIdx.y * blockDim.x + threadIdx.x;
+  if (u >= rs) return;
+  inv_targets_item(RX, RZ, rs, n, k, colx, pp, part, rows_per_chunk, blockIdx.x, u);
+}
+
+__global__ void __launch_bounds__(256)
+inv_combine_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint64_t *__restrict__ qsig,
+                   uint32_t rs, uint32_t k, const int64_t *__restrict__ mst,
+                   const uint64_t *__restrict__ part, uint32_t chunks) {
+  __shared__ uint64_t red[6][8][32];
+  const int64_t pp = mst[kMsPivot];
+  if (pp == kInvNoPivot) return;
+  inv_combine_group(RX, RZ, qsig, rs, k, pp, part, chunks, blockIdx.x, red);
 }
 
 __global__ void __launch_bounds__(1024)
@@ -357,50 +436,7 @@ inv_finalize_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint64
                     uint8_t *__restrict__ record, uint8_t *__restrict__ kinds) {
   const uint32_t q = qubits[qi];
   if (q >= n) return;  // flagged by the gather
-  const int64_t pp = mst[kMsPivot];
-  const uint32_t tid = threadIdx.x;
-  if (pp == kInvNoPivot) {  // deterministic: the outcome is S_S[q]
-    if (tid == 0) {
-      record[midx] = (uint8_t)((qsig[q >> 6] >> (q & 63)) & 1u);
-      kinds[midx] = 0;
-    }
-    return;
-  }
-  const uint64_t lo = 64ull * k;
-  const uint64_t p = (uint64_t)(pp - (int64_t)lo);
-  uint64_t *xs = RX + (lo + p) * rs, *xd = RX + p * rs, *zs = RZ + (lo + p) * rs, *zd = RZ + p * rs;
-  // Y case (the pivot's destabilizer has z at q in the Z_q image): H_YZ, else H
-  const bool yz = ((xd[q >> 6] >> (q & 63)) & 1u) != 0;
-  __syncthreads();  // every thread has read xd[q >> 6] before it changes
-  for (uint32_t u = tid; u < rs; u += blockDim.x) {
-    uint64_t a = xs[u], b = xd[u], c = zs[u], e = zd[u];
-    if (yz) {
-      qsig[u] ^= a & ~b;
-      a ^= b;
-      qsig[rs + u] ^= c & ~e;
-      c ^= e;
-    } else {
-      qsig[u] ^= a & b;
-      uint64_t t = a; a = b; b = t;
-      qsig[rs + u] ^= c & e;
-      t = c; c = e; e = t;
-    }
-    xs[u] = a; xd[u] = b; zs[u] = c; zd[u] = e;
-  }
-  __syncthreads();
-  const uint32_t coin = (uint32_t)(philox4x64_10(midx, shot, 0, 0, seed, kCoinKey).v[0] & 1u);
-  const uint32_t sq = (uint32_t)((qsig[q >> 6] >> (q & 63)) & 1u);
-  __syncthreads();  // every thread has read S_S[q] before the X injection changes it
-  if (sq != coin)
-    for (uint32_t u = tid; u < rs; u += blockDim.x) {
-      qsig[u] ^= xd[u];
-      qsig[rs + u] ^= zd[u];
-    }
-  if (tid == 0) {
-    record[midx] = (uint8_t)coin;
-    kinds[midx] = 1;
-    mst[kMsPivot] = kInvNoPivot;
-  }
+  inv_finalize_block(RX, RZ, qsig, rs, k, q, mst[kMsPivot], mst, midx, seed, shot, record, kinds);
 }
 
 size_t inv_scratch_words(const Layout &L) { return (size_t)6 * kInvChunks * L.rs; }
