@@ -30,7 +30,7 @@ namespace qs {
 
 constexpr int kDetBlocks = 152;     // chunks of the deterministic product (one per SM)
 constexpr int kMeasStateWords = 16; // per-measurement device state
-constexpr int kInvChunks = 256;     // row chunks of the inverse-mode target pass
+constexpr int kInvChunks = 512;     // row chunks of the inverse-mode target pass
 
 // device error flags (sticky, cleared by reset)
 enum : uint32_t {

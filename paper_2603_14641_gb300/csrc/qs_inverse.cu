@@ -300,21 +300,25 @@ __device__ __forceinline__ void inv_targets_item(uint64_t *__restrict__ RX, uint
 
 // Chunk partials merge in index order: (D, L, F) of an earlier range followed
 // by (D', L', F') of a later one is (D ^ D', L ^ L' ^ (D & D'), F ^ F'), the
-// pairs across the two ranges being D & D'. A block of 8 warps covers 32
-// words (lane = word, coalesced rows of the partials): warp w merges chunks
-// 32 w .. 32 w + 31 in order, then warp 0 merges the 8 warps' results in
-// order. Called by every thread of the block (it holds a block barrier).
+// pairs across the two ranges being D & D'. A block of 32 warps covers 32
+// words (lane = word, coalesced rows of the partials): warp w merges its
+// consecutive run of chunks in order, then warp 0 merges the 32 warps' results
+// in order. Called by every thread of the block (it holds a block barrier).
+constexpr int kCombineWarps = 32;
+
 __device__ __forceinline__ void inv_combine_group(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ,
                                                   uint64_t *__restrict__ qsig, uint32_t rs, uint32_t k,
                                                   int64_t pp, const uint64_t *__restrict__ part,
-                                                  uint32_t chunks, uint32_t group, uint64_t (*red)[8][32]) {
+                                                  uint32_t chunks, uint32_t group,
+                                                  uint64_t (*red)[kCombineWarps][32]) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t u = group * 32 + lane;
+  const uint32_t per = (chunks + kCombineWarps - 1) / kCombineWarps;
   uint64_t px = 0, pz = 0, fx = 0, fz = 0, lx = 0, lz = 0;
   if (u < rs) {
-    const uint32_t c1 = min(chunks, 32 * (warp + 1));
+    const uint32_t c1 = min(chunks, per * (warp + 1));
 #pragma unroll 4
-    for (uint32_t c = 32 * warp; c < c1; ++c) {
+    for (uint32_t c = per * warp; c < c1; ++c) {
       const uint64_t *o = part + (size_t)6 * c * rs + u;
       const uint64_t dx = *(o), dz = *(o + rs);
       fx ^= *(o + 2 * (size_t)rs);
@@ -330,7 +334,7 @@ __device__ __forceinline__ void inv_combine_group(uint64_t *__restrict__ RX, uin
   __syncthreads();
   if (warp == 0 && u < rs) {
     px = pz = fx = fz = lx = lz = 0;
-    for (uint32_t w = 0; w < 8; ++w) {
+    for (uint32_t w = 0; w < kCombineWarps; ++w) {
       const uint64_t dx = red[0][w][lane], dz = red[1][w][lane];
       fx ^= red[2][w][lane];
       fz ^= red[3][w][lane];
@@ -347,7 +351,6 @@ __device__ __forceinline__ void inv_combine_group(uint64_t *__restrict__ RX, uin
     qsig[u] = *(qsig + u) ^ fx ^ (xsp & lx);
     qsig[rs + u] = *(qsig + rs + u) ^ fz ^ (zsp & lz);
   }
-  __syncthreads();  // red is reused by the block's next group
 }
 
 // One block: the H or H_YZ injection on the pivot, then the X injection when
@@ -419,11 +422,11 @@ inv_targets_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_
   inv_targets_item(RX, RZ, rs, n, k, colx, pp, part, rows_per_chunk, blockIdx.x, u);
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * kCombineWarps)
 inv_combine_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint64_t *__restrict__ qsig,
                    uint32_t rs, uint32_t k, const int64_t *__restrict__ mst,
                    const uint64_t *__restrict__ part, uint32_t chunks) {
-  __shared__ uint64_t red[6][8][32];
+  __shared__ uint64_t red[6][kCombineWarps][32];  // 48 KB
   const int64_t pp = mst[kMsPivot];
   if (pp == kInvNoPivot) return;
   inv_combine_group(RX, RZ, qsig, rs, k, pp, part, chunks, blockIdx.x, red);
@@ -450,8 +453,8 @@ cudaError_t launch_inv_measure_one(const Dev &d, const uint32_t *qubits, uint32_
   const uint32_t tt = std::min<uint32_t>(256, (L.rs + 31) / 32 * 32);  // no idle warps when rs < 256
   inv_targets_kernel<<<dim3(chunks, (L.rs + tt - 1) / tt), tt, 0, s>>>(d.RX, d.RZ, L.rs, L.n, L.k, d.colx,
                                                                       d.mst, d.inv_part, rows_per_chunk);
-  inv_combine_kernel<<<(L.rs + 31) / 32, 256, 0, s>>>(d.RX, d.RZ, d.qsig, L.rs, L.k, d.mst, d.inv_part,
-                                                     chunks);
+  inv_combine_kernel<<<(L.rs + 31) / 32, 32 * kCombineWarps, 0, s>>>(d.RX, d.RZ, d.qsig, L.rs, L.k, d.mst,
+                                                                    d.inv_part, chunks);
   inv_finalize_kernel<<<1, 1024, 0, s>>>(d.RX, d.RZ, d.qsig, L.rs, L.n, L.k, qubits, i, d.mst, midx,
                                          key.seed, key.shot, d.record, d.kinds);
   if (launches) *launches += 4;
