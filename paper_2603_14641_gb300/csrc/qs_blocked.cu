@@ -39,6 +39,13 @@ constexpr int64_t kBlkNone = LLONG_MAX;
 constexpr int32_t kBaseOrig = -1;
 constexpr int32_t kBasePivot = 1000;  // base = kBasePivot + j: pivot row of step j
 constexpr int kCW = 32;               // column words per phase-3 chunk
+// windows of the lazy symbolic pass: stabilizer rows per window = threads of its
+// CTA. 256 took the pass from 30.9 to 23.8 ms per step on the 10k workload and
+// from 0.56 to 0.45 ms at 180k against 1,024 (512: 24.3 and 0.47 ms): a step
+// waits on barriers of 8 warps instead of 32.
+constexpr int kLazyLog2 = 8;
+constexpr int kLazyThreads = 1 << kLazyLog2;
+constexpr uint32_t kLazyMaxWindows = (1u << 20) >> kLazyLog2;  // n <= 2^20
 
 struct BlkState {
   int64_t slot[3];     // pivot search results, rotating
@@ -54,7 +61,7 @@ struct BlkState {
   uint64_t cpiv[64];   // C of the pivot row at its step (lazy symbolic pass)
   uint32_t err;
   uint32_t pad2;
-  uint64_t win_or[1024];  // OR of C over each window of 1024 stabilizer rows (lazy pass)
+  uint64_t win_or[4096];  // OR of C over each window of stabilizer rows (lazy pass)
 };
 
 __device__ __forceinline__ int m4(int v) { return ((v % 4) + 4) % 4; }
@@ -93,12 +100,12 @@ blk_init_kernel(const uint64_t *__restrict__ RX, uint32_t rs, uint64_t nrows, ui
     base[r] = kBaseOrig;
   }
   {
-    // OR of C over this warp's 32 rows (one window of 1024 stabilizer rows: the
+    // OR of C over this warp's 32 rows (in one window of stabilizer rows: the
     // stabilizer half starts at 64 k, a multiple of 32)
     uint64_t o = (r >= 64ull * k && r < 64ull * k + n) ? c : 0;
     for (int d = 16; d > 0; d >>= 1) o |= __shfl_xor_sync(0xffffffffu, o, d);
     if ((threadIdx.x & 31) == 0 && o)
-      atomicOr(reinterpret_cast<unsigned long long *>(&st->win_or[(r - 64ull * k) >> 10]), o);
+      atomicOr(reinterpret_cast<unsigned long long *>(&st->win_or[(r - 64ull * k) >> kLazyLog2]), o);
   }
   const uint32_t ball = __ballot_sync(0xffffffffu, (c & 1ull) != 0);
   if ((threadIdx.x & 31) == 0 && r < nrows) {
@@ -166,7 +173,7 @@ blk_step_kernel(uint64_t nrows, uint32_t n, uint32_t k, int j, int B, const uint
 // (p_j, C_{p_j}) is needed here (blk_replay_kernel then derives every row's M_r
 // and base_r from it), and the pivot of step j is the first stabilizer row, in
 // index order, whose current C has bit j. So the stabilizer rows are scanned in
-// windows of 1024 (one row per thread), in order, and a window's rows are
+// windows of kLazyThreads (one row per thread), in order, and a window's rows are
 // brought up to step j (replaying steps a_w..j-1 on them: the pivot row of a
 // step becomes 0, a row with bit s set takes ^= C_{p_s}) only when it can hold
 // bit j. That is decided from U_w, an upper bound on the OR of the window's C:
@@ -176,8 +183,6 @@ blk_step_kernel(uint64_t nrows, uint32_t n, uint32_t k, int j, int B, const uint
 // window and one barrier; rows far from the front are never read. Rows of
 // replayed windows live in a working copy (W, the second C buffer); C0 stays
 // intact for the replay kernel.
-constexpr int kLazyThreads = 1024;
-constexpr uint32_t kLazyMaxWindows = 1024;  // n <= 2^20
 
 __device__ __forceinline__ uint64_t lazy_bound(uint64_t u, int a, int j, const uint64_t *cp) {
   for (int s = a; s < j; ++s)
@@ -196,12 +201,17 @@ blk_lazy_symbolic_kernel(uint32_t n, uint32_t k, int B, const uint64_t *__restri
   __shared__ uint32_t srow[2][32];           // per warp: first row with bit j (or ~0u)
   __shared__ uint64_t sval[2][32], sor[2][32];
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t nwin = (n + 1023) / 1024;
+  const uint32_t nwin = (n + kLazyThreads - 1) >> kLazyLog2;
   const uint64_t lo = 64ull * k;
   for (uint32_t w = tid; w < nwin; w += kLazyThreads) {
     su[w] = st->win_or[w];
     sa[w] = 0;
     sinit[w] = 0;
+  }
+  if (tid < 64) {  // slots of warps the block does not have stay empty
+    srow[tid >> 5][tid & 31] = 0xFFFFFFFFu;
+    sval[tid >> 5][tid & 31] = 0;
+    sor[tid >> 5][tid & 31] = 0;
   }
   __syncthreads();
   uint32_t front = 0;  // first window that may hold a nonzero row (uniform)
@@ -215,8 +225,8 @@ blk_lazy_symbolic_kernel(uint32_t n, uint32_t k, int B, const uint64_t *__restri
     for (uint32_t w = front; w < nwin; ++w) {
       const int a = sa[w];
       if (!((lazy_bound(su[w], a, j, scp) >> j) & 1ull)) continue;  // no row can have bit j
-      // bring row 1024 w + tid up to step j
-      const uint32_t i = w * 1024 + tid;
+      // bring row kLazyThreads w + tid up to step j
+      const uint32_t i = w * kLazyThreads + tid;
       uint64_t c = 0;
       if (i < n) {
         if (cw == w) c = cc;
@@ -225,7 +235,7 @@ blk_lazy_symbolic_kernel(uint32_t n, uint32_t k, int B, const uint64_t *__restri
           if ((int32_t)i == spiv[s2]) c = 0;
           else if ((c >> s2) & 1ull) c ^= scp[s2];
         }
-        if (cw != w && cw != 0xFFFFFFFFu) W[lo + cw * 1024 + tid] = cc;  // evict the held row
+        if (cw != w && cw != 0xFFFFFFFFu) W[lo + cw * kLazyThreads + tid] = cc;  // evict the held row
         cw = w;
         cc = c;
       }
@@ -256,7 +266,7 @@ blk_lazy_symbolic_kernel(uint32_t n, uint32_t k, int B, const uint64_t *__restri
         sinit[w] = 1;
       }
       if (best != 0xFFFFFFFFu) {
-        hit = w * 1024 + best;
+        hit = w * kLazyThreads + best;
         hitc = bc;
         break;
       }
@@ -889,7 +899,7 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   });
   if (ea != cudaSuccess) return ea;
   tbegin(d.timer, QS_TIME_BLK_SYMBOLIC, s);
-  const uint32_t nwin = (L.n + 1023) / 1024;
+  const uint32_t nwin = (L.n + kLazyThreads - 1) >> kLazyLog2;
   blk_reset_kernel<<<1, 256, 0, s>>>(st, B, nwin);
   blk_init_kernel<<<rb, 256, 0, s>>>(d.RX, L.rs, L.nrows, L.n, L.k, qubits, B, C0, M, base, st,
                                      d.err);
