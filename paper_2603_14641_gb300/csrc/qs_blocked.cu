@@ -686,8 +686,12 @@ __device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t nrows, uin
   if (lane == 0) Tp[tp0 + r] = (v >> 6) * 2 + (v & 1);
 }
 
+// 1,024 threads at 64 registers: 6.80 ms per dense block at 180k, against
+// 7.46 ms with 768 threads (80 registers) and 9.55 ms with 512 (100)
+constexpr int kApplyThreads = 1024;
+
 template <typename Idx>
-__global__ void __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(kApplyThreads, 1)
 blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t rs, uint32_t nrows,
                     const uint32_t *__restrict__ qubits, const uint64_t *__restrict__ VX,
                     const uint64_t *__restrict__ VZ, const uint4 *__restrict__ list,
@@ -705,11 +709,11 @@ blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t 
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // shared tables, one thread per (group, quarter of its entries, word): the
+  // shared tables, one item per (group, quarter of its entries, word): the
   // quarter's two top steps give its first entry, then its entries follow in
-  // Gray-code order, each one V row away from the previous (blockDim = 1024)
-  {
-    const int w = threadIdx.x & 31, sr = (threadIdx.x >> 5) & 3, g = threadIdx.x >> 7;
+  // Gray-code order, each one V row away from the previous
+  for (int it = threadIdx.x; it < kSmemGroups * 4 * 32; it += blockDim.x) {
+    const int w = it & 31, sr = (it >> 5) & 3, g = it >> 7;
     const int nb = smem_group_bits(g), e0 = smem_group_base(g) + (sr << (nb - 2));
     ulonglong2 vv[6];
 #pragma unroll
@@ -927,10 +931,10 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
       1, (uint32_t)std::min<uint64_t>(((uint64_t)d.sms * 8 + chunks - 1) / chunks, L.nrows / 512));
   tbegin(d.timer, QS_TIME_BLK_APPLY, s);
   if (!d.wide_offsets && (uint64_t)L.nrows * L.rs < (1ull << 32))
-    blk_apply_kernel<uint32_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
+    blk_apply_kernel<uint32_t><<<dim3(chunks, rows_y), kApplyThreads, smem, s>>>(
         d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, list, Tp, st);
   else
-    blk_apply_kernel<uint64_t><<<dim3(chunks, rows_y), 1024, smem, s>>>(
+    blk_apply_kernel<uint64_t><<<dim3(chunks, rows_y), kApplyThreads, smem, s>>>(
         d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, list, Tp, st);
   tend(d.timer, QS_TIME_BLK_APPLY, s);
   tbegin(d.timer, QS_TIME_BLK_SIGNS, s);
