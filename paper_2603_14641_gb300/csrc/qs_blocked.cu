@@ -631,11 +631,11 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 template <typename Idx>
-__device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t nrows, uint64_t *RX,
-                                             uint64_t *RZ, bool ok, uint32_t word,
-                                             const uint32_t *qubits, const uint64_t *VX,
-                                             const uint64_t *VZ, uint32_t rs, uint32_t lane,
-                                             const char *tb, uint32_t tq, int32_t *Tp, uint64_t tp0) {
+__device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t nrows, uint64_t *RX, uint64_t *RZ,
+                                          bool ok, uint32_t word, const uint32_t *qubits,
+                                          const uint64_t *VX, const uint64_t *VZ, uint32_t rs,
+                                          uint32_t lane, const char *tb, uint32_t tq, int32_t *Tp,
+                                          uint64_t tp0) {
   const uint32_t r = a.r;
   if (r >= nrows) return;  // uniform over the warp
   const Idx off = (Idx)r * rs + word;
@@ -693,9 +693,9 @@ constexpr int kApplyThreads = 1024;
 template <typename Idx>
 __global__ void __launch_bounds__(kApplyThreads, 1)
 blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t rs, uint32_t nrows,
-                    const uint32_t *__restrict__ qubits, const uint64_t *__restrict__ VX,
-                    const uint64_t *__restrict__ VZ, const uint4 *__restrict__ list,
-                    int32_t *__restrict__ Tp, const BlkState *st) {
+                 const uint32_t *__restrict__ qubits, const uint64_t *__restrict__ VX,
+                 const uint64_t *__restrict__ VZ, const uint4 *__restrict__ list,
+                 int32_t *__restrict__ Tp, const BlkState *st) {
   extern __shared__ ulonglong2 T[];  // [kSmemEntries][kCW] of (x word, z word)
   __shared__ uint32_t s_tmem;
   const int L = st->len;
