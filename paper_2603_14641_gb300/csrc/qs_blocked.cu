@@ -51,6 +51,9 @@ struct BlkState {
   int64_t slot[3];     // pivot search results, rotating
   int32_t len;         // steps completed in this block
   uint32_t ntouched;   // rows the block changes (entries of the apply pass's row list)
+  uint32_t i0;         // first measurement of the block within its window
+  int32_t B;           // measurements the block attempts (0 past the window's end)
+  uint32_t cursor;     // next measurement of the window: read by the next block's reset
   int64_t piv[64];     // pivot row of each step
   uint64_t mpiv[64];   // steps that targeted the pivot row before it became pivot
   int32_t A[64];       // |x_V & z_V| mod 4 (summed over words)
@@ -66,10 +69,14 @@ struct BlkState {
 
 __device__ __forceinline__ int m4(int v) { return ((v % 4) + 4) % 4; }
 
-__global__ void blk_reset_kernel(BlkState *st, int B, uint32_t nwin) {
+// the block starts where the previous block of the window stopped (st->cursor),
+// so the host can enqueue several blocks before it reads how far they got
+__global__ void blk_reset_kernel(BlkState *st, uint32_t count, uint32_t nwin) {
   const int t = threadIdx.x;
+  const uint32_t i0 = st->cursor;
+  const int B = i0 < count ? (int)min(64u, count - i0) : 0;
   if (t < 3) st->slot[t] = kBlkNone;
-  if (t == 0) { st->len = B; st->err = 0; st->ntouched = 0; }
+  if (t == 0) { st->len = B; st->err = 0; st->ntouched = 0; st->i0 = i0; st->B = B; }
   if (t < 64) {
     st->piv[t] = kBlkNone; st->mpiv[t] = 0; st->A[t] = 0; st->B0[t] = 0; st->Cp[t] = 0;
     st->rV[t] = 0; st->G[t] = 0;
@@ -81,9 +88,11 @@ __global__ void blk_reset_kernel(BlkState *st, int B, uint32_t nwin) {
 // pivot of step 0 by atomicMin
 __global__ void __launch_bounds__(256)
 blk_init_kernel(const uint64_t *__restrict__ RX, uint32_t rs, uint64_t nrows, uint32_t n, uint32_t k,
-                const uint32_t *__restrict__ qubits, int B, uint64_t *__restrict__ C,
+                const uint32_t *__restrict__ window, uint64_t *__restrict__ C,
                 uint64_t *__restrict__ M, int32_t *__restrict__ base, BlkState *st,
                 uint32_t *__restrict__ err) {
+  const int B = st->B;
+  const uint32_t *qubits = window + st->i0;
   const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t c = 0;
   if (r < nrows) {
@@ -121,10 +130,11 @@ blk_init_kernel(const uint64_t *__restrict__ RX, uint32_t rs, uint64_t nrows, ui
 
 // symbolic step j: Cin -> Cout
 __global__ void __launch_bounds__(256)
-blk_step_kernel(uint64_t nrows, uint32_t n, uint32_t k, int j, int B, const uint64_t *__restrict__ Cin,
+blk_step_kernel(uint64_t nrows, uint32_t n, uint32_t k, int j, const uint64_t *__restrict__ Cin,
                 uint64_t *__restrict__ Cout, uint64_t *__restrict__ M, int32_t *__restrict__ base,
                 BlkState *st) {
   if (j >= st->len) return;
+  const int B = st->B;
   const int64_t p = st->slot[j % 3];
   if (p == kBlkNone) {
     if (blockIdx.x == 0 && threadIdx.x == 0) st->len = j;
@@ -191,8 +201,9 @@ __device__ __forceinline__ uint64_t lazy_bound(uint64_t u, int a, int j, const u
 }
 
 __global__ void __launch_bounds__(kLazyThreads)
-blk_lazy_symbolic_kernel(uint32_t n, uint32_t k, int B, const uint64_t *__restrict__ C0,
+blk_lazy_symbolic_kernel(uint32_t n, uint32_t k, const uint64_t *__restrict__ C0,
                          uint64_t *__restrict__ W, BlkState *st) {
+  const int B = st->B;
   __shared__ uint64_t su[kLazyMaxWindows];   // U_w
   __shared__ uint8_t sa[kLazyMaxWindows];    // a_w: steps replayed on the window's rows
   __shared__ uint8_t sinit[kLazyMaxWindows]; // rows already in the working copy
@@ -693,12 +704,14 @@ constexpr int kApplyThreads = 1024;
 template <typename Idx>
 __global__ void __launch_bounds__(kApplyThreads, 1)
 blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t rs, uint32_t nrows,
-                 const uint32_t *__restrict__ qubits, const uint64_t *__restrict__ VX,
+                 const uint32_t *__restrict__ window, const uint64_t *__restrict__ VX,
                  const uint64_t *__restrict__ VZ, const uint4 *__restrict__ list,
                  int32_t *__restrict__ Tp, const BlkState *st) {
   extern __shared__ ulonglong2 T[];  // [kSmemEntries][kCW] of (x word, z word)
   __shared__ uint32_t s_tmem;
   const int L = st->len;
+  if (L == 0) return;  // a block enqueued past the window's end or behind a deterministic step
+  const uint32_t *qubits = window + st->i0;
   const uint32_t u0 = blockIdx.x * kCW;  // first column word of the chunk
   const uint32_t nw = min((uint32_t)kCW, rs - u0);
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -810,14 +823,14 @@ blk_apply_kernel(uint64_t *__restrict__ RX, uint64_t *__restrict__ RZ, uint32_t 
 
 // per row: new sign from the accumulated terms; pivot rows get their coin; record
 __global__ void __launch_bounds__(256)
-blk_rows_kernel(uint64_t *__restrict__ S, uint64_t nrows, const uint32_t *__restrict__ qubits,
-                const uint64_t *__restrict__ M, const int32_t *__restrict__ base,
-                const int32_t *__restrict__ Tp, uint32_t chunks, const BlkState *st, uint64_t m0,
-                uint64_t seed,
-                uint64_t shot, uint8_t *__restrict__ record, uint8_t *__restrict__ kinds,
-                uint32_t *__restrict__ err) {
+blk_rows_kernel(uint64_t *__restrict__ S, uint64_t nrows, const uint64_t *__restrict__ M,
+                const int32_t *__restrict__ base, const int32_t *__restrict__ Tp, uint32_t chunks,
+                BlkState *st, uint64_t window_m0, uint64_t seed, uint64_t shot,
+                uint8_t *__restrict__ record, uint8_t *__restrict__ kinds, uint32_t *__restrict__ err) {
   const int L = st->len;
+  const uint64_t m0 = window_m0 + st->i0;  // record index of the block's first measurement
   const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r == 0) st->cursor = st->i0 + (uint32_t)L;  // the next block starts here
   if (r < (uint64_t)L) {
     const uint32_t b = (uint32_t)(philox4x64_10(m0 + r, shot, 0, 0, seed, kCoinKey).v[0] & 1u);
     record[m0 + r] = (uint8_t)b;
@@ -872,9 +885,8 @@ static std::atomic<uint64_t> g_apply_attr_set{0};
 
 // Enqueues one block of up to 64 measurements; the number actually done is
 // st->len (read by the host after the stream is synchronised).
-cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qubits, int B,
-                                 uint64_t m0, qs_key key, cudaStream_t s, int *launches,
-                                 int32_t **len_dev) {
+cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *window, uint32_t count,
+                                 uint64_t m0, qs_key key, cudaStream_t s, int *launches) {
   const Layout &L = d.L;
   uint8_t *p = static_cast<uint8_t *>(scratch);
   auto take = [&](size_t bytes) { uint8_t *q = p; p += (bytes + 255) & ~size_t(255); return q; };
@@ -904,18 +916,17 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   if (ea != cudaSuccess) return ea;
   tbegin(d.timer, QS_TIME_BLK_SYMBOLIC, s);
   const uint32_t nwin = (L.n + kLazyThreads - 1) >> kLazyLog2;
-  blk_reset_kernel<<<1, 256, 0, s>>>(st, B, nwin);
-  blk_init_kernel<<<rb, 256, 0, s>>>(d.RX, L.rs, L.nrows, L.n, L.k, qubits, B, C0, M, base, st,
-                                     d.err);
-  int sym_launches = B;
+  blk_reset_kernel<<<1, 256, 0, s>>>(st, count, nwin);
+  blk_init_kernel<<<rb, 256, 0, s>>>(d.RX, L.rs, L.nrows, L.n, L.k, window, C0, M, base, st, d.err);
+  int sym_launches = 64;
   if (!d.step_symbolic) {
-    blk_lazy_symbolic_kernel<<<1, kLazyThreads, 0, s>>>(L.n, L.k, B, C0, C1, st);
+    blk_lazy_symbolic_kernel<<<1, kLazyThreads, 0, s>>>(L.n, L.k, C0, C1, st);
     blk_replay_kernel<<<rb, 256, 0, s>>>(L.nrows, L.k, C0, M, base, st);
     sym_launches = 2;
   } else {
-    for (int j = 0; j < B; ++j)
-      blk_step_kernel<<<rb, 256, 0, s>>>(L.nrows, L.n, L.k, j, B, (j & 1) ? C1 : C0,
-                                         (j & 1) ? C0 : C1, M, base, st);
+    for (int j = 0; j < 64; ++j)  // steps past the block's length return at once
+      blk_step_kernel<<<rb, 256, 0, s>>>(L.nrows, L.n, L.k, j, (j & 1) ? C1 : C0, (j & 1) ? C0 : C1, M,
+                                         base, st);
   }
   tend(d.timer, QS_TIME_BLK_SYMBOLIC, s);
   tbegin(d.timer, QS_TIME_BLK_PIVOT_ROWS, s);
@@ -932,18 +943,34 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qu
   tbegin(d.timer, QS_TIME_BLK_APPLY, s);
   if (!d.wide_offsets && (uint64_t)L.nrows * L.rs < (1ull << 32))
     blk_apply_kernel<uint32_t><<<dim3(chunks, rows_y), kApplyThreads, smem, s>>>(
-        d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, list, Tp, st);
+        d.RX, d.RZ, L.rs, (uint32_t)L.nrows, window, VX, VZ, list, Tp, st);
   else
     blk_apply_kernel<uint64_t><<<dim3(chunks, rows_y), kApplyThreads, smem, s>>>(
-        d.RX, d.RZ, L.rs, (uint32_t)L.nrows, qubits, VX, VZ, list, Tp, st);
+        d.RX, d.RZ, L.rs, (uint32_t)L.nrows, window, VX, VZ, list, Tp, st);
   tend(d.timer, QS_TIME_BLK_APPLY, s);
   tbegin(d.timer, QS_TIME_BLK_SIGNS, s);
-  blk_rows_kernel<<<rb, 256, 0, s>>>(d.S, L.nrows, qubits, M, base, Tp, chunks, st, m0, key.seed,
-                                     key.shot, d.record, d.kinds, d.err);
+  blk_rows_kernel<<<rb, 256, 0, s>>>(d.S, L.nrows, M, base, Tp, chunks, st, m0, key.seed, key.shot,
+                                     d.record, d.kinds, d.err);
   tend(d.timer, QS_TIME_BLK_SIGNS, s);
   if (launches) *launches += 7 + sym_launches;
-  if (len_dev) *len_dev = &st->len;
   return cudaGetLastError();
 }
+
+__global__ void blk_set_cursor_kernel(BlkState *st, uint32_t v) { st->cursor = v; }
+
+static BlkState *blk_state(const Layout &L, void *scratch) {
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return reinterpret_cast<BlkState *>(static_cast<uint8_t *>(scratch) + 3 * al(L.nrows * 8) +
+                                      al(L.nrows * 4) + al((size_t)blk_chunks(L) * L.nrows * 4) +
+                                      2 * al(64ull * L.rs * 8));
+}
+
+cudaError_t set_block_cursor(const Layout &L, void *scratch, uint32_t v, cudaStream_t s) {
+  blk_set_cursor_kernel<<<1, 1, 0, s>>>(blk_state(L, scratch), v);
+  return cudaGetLastError();
+}
+
+const uint32_t *block_cursor(const Layout &L, void *scratch) { return &blk_state(L, scratch)->cursor; }
+
 
 }  // namespace qs

@@ -242,12 +242,17 @@ cudaError_t launch_inv_measure_one(const Dev &d, const uint32_t *qubits, uint32_
 bool measure_window_supported(const Layout &L);
 cudaError_t launch_measure_window(const Dev &d, const uint32_t *qubits, uint32_t count,
                                   uint64_t m0, qs_key key, cudaStream_t s, int *launches);
-// blocked measurement of up to 64 qubits (scratch of blocked_scratch_bytes);
-// *len_dev receives the device address of the count actually measured
+// blocked measurement (scratch of blocked_scratch_bytes): one block measures up
+// to 64 qubits of a window of count (record indices from m0), starting at the
+// window position the scratch's cursor holds, and moves the cursor past the
+// steps it measured (it stops before a deterministic outcome); blocks can be
+// enqueued back to back. block_cursor gives the cursor's device address,
+// set_block_cursor sets it on the stream.
 size_t blocked_scratch_bytes(const Layout &L);
-cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *qubits, int B,
-                                 uint64_t m0, qs_key key, cudaStream_t s, int *launches,
-                                 int32_t **len_dev);
+cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *window, uint32_t count,
+                                 uint64_t m0, qs_key key, cudaStream_t s, int *launches);
+cudaError_t set_block_cursor(const Layout &L, void *scratch, uint32_t v, cudaStream_t s);
+const uint32_t *block_cursor(const Layout &L, void *scratch);
 // fused segment of L layers on a word-sliced, shared-memory-resident tableau
 // (S == nullptr: frames, no signs); lptr: L + 1 device gate offsets
 bool fused_fits(uint32_t n);

@@ -518,9 +518,16 @@ static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint6
     // outcome, which then goes through the single-measurement path. After two
     // blocks in a row that stop at their first step (a run of deterministic
     // outcomes), the rest of the window takes the pipelined path.
-    uint32_t i = 0, empty_blocks = 0;
+    // Each block starts at the window position a device cursor holds and moves
+    // it on, so rounds of several blocks go out before the host reads how far
+    // they got: one round doubles (up to 8 blocks) while rounds finish, and
+    // drops back to one block after a block stopped short.
+    const uint32_t *cur = block_cursor(s->d.L, s->blk);
+    QS_CUDA(s, set_block_cursor(s->d.L, s->blk, 0, s->stream));
+    s->launches += 1;
+    uint32_t i = 0, empty_rounds = 0, per_round = 1;
     while (i < count) {
-      if (empty_blocks >= 2) {
+      if (empty_rounds >= 2) {
         int l = 0;
         tbegin(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
         QS_CUDA(s, launch_measure_window(s->d, qdev + i, count - i, m0 + i, key, s->stream, &l));
@@ -528,27 +535,37 @@ static int measure_staged(qs_sim *s, const uint32_t *qdev, uint32_t count, uint6
         s->launches += (uint64_t)l;
         break;
       }
-      Range block_range("blocked measurement block");
-      const int B = (int)std::min<uint32_t>(64, count - i);
-      int l = 0;
-      int32_t *len_dev = nullptr;
-      QS_CUDA(s, launch_measure_block(s->d, s->blk, qdev + i, B, m0 + i, key, s->stream, &l, &len_dev));
-      s->launches += (uint64_t)l;
-      int32_t done = 0;
-      QS_CUDA(s, cudaMemcpyAsync(&done, len_dev, 4, cudaMemcpyDeviceToHost, s->stream));
+      Range block_range("blocked measurement round");
+      const uint32_t nb = std::min<uint32_t>(per_round, (count - i + 63) / 64);
+      for (uint32_t b = 0; b < nb; ++b) {
+        int l = 0;
+        QS_CUDA(s, launch_measure_block(s->d, s->blk, qdev, count, m0, key, s->stream, &l));
+        s->launches += (uint64_t)l;
+      }
+      uint32_t at = 0;
+      QS_CUDA(s, cudaMemcpyAsync(&at, cur, 4, cudaMemcpyDeviceToHost, s->stream));
       QS_CUDA(s, cudaStreamSynchronize(s->stream));
       if (s->timer) s->timer->resolve();
-      if (done < 0 || done > B) return fail(QS_ERR_INTERNAL, "blocked measurement length");
-      i += (uint32_t)done;
-      if (done < B) {
-        l = 0;
+      if (at < i || at > count) return fail(QS_ERR_INTERNAL, "blocked measurement cursor");
+      const uint32_t done = at - i;
+      i = at;
+      if (i < count && done < 64 * nb) {
+        // a block stopped before a deterministic outcome (the blocks after it
+        // in the round did nothing): measure it alone and step past it
+        int l = 0;
         tbegin(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
         QS_CUDA(s, launch_measure_window(s->d, qdev + i, 1, m0 + i, key, s->stream, &l));
         tend(s->d.timer, QS_TIME_MEASURE_SINGLE, s->stream);
         s->launches += (uint64_t)l;
         i += 1;
+        QS_CUDA(s, set_block_cursor(s->d.L, s->blk, i, s->stream));
+        s->launches += 1;
+        empty_rounds = done == 0 ? empty_rounds + 1 : 0;
+        per_round = 1;
+      } else {
+        empty_rounds = 0;
+        per_round = std::min<uint32_t>(8, 2 * per_round);
       }
-      empty_blocks = done == 0 ? empty_blocks + 1 : 0;
     }
     return QS_OK;
   }
