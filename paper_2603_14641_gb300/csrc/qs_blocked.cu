@@ -96,13 +96,24 @@ blk_init_kernel(const uint64_t *__restrict__ RX, uint32_t rs, uint64_t nrows, ui
   const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t c = 0;
   if (r < nrows) {
-    uint32_t lastw = 0xFFFFFFFFu;
-    uint64_t word = 0;
-    for (int j = 0; j < B; ++j) {
-      const uint32_t q = qubits[j];
-      if (q >= n) { if (r == 0) atomicOr(err, kErrBadQubit); continue; }
-      if ((q >> 6) != lastw) { lastw = q >> 6; word = RX[r * rs + lastw]; }
-      c |= ((word >> (q & 63)) & 1ull) << j;
+    // eight steps' words loaded before any is used (independent loads in flight)
+    for (int j0 = 0; j0 < B; j0 += 8) {
+      uint32_t qq[8];
+      uint64_t wv[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        qq[t] = j0 + t < B ? qubits[j0 + t] : n;
+        wv[t] = qq[t] < n ? RX[r * rs + (qq[t] >> 6)] : 0;
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (j0 + t >= B) break;
+        if (qq[t] >= n) {
+          if (r == 0) atomicOr(err, kErrBadQubit);
+          continue;
+        }
+        c |= ((wv[t] >> (qq[t] & 63)) & 1ull) << (j0 + t);
+      }
     }
     C[r] = c;
     M[r] = 0;
@@ -361,8 +372,11 @@ blk_vrows_kernel(const uint64_t *__restrict__ RX, const uint64_t *__restrict__ R
     oz[j][lane] = in ? RZ[p * rs + u] : 0;
   }
   if (w == 0) {
+    // the steps' target masks, loaded once (lane l: steps l and l + 32) rather
+    // than one dependent global load per step of the loop below
+    const uint64_t mlo = lane < L ? st->mpiv[lane] : 0, mhi = lane + 32 < L ? st->mpiv[lane + 32] : 0;
     for (int j = 0; j < L; ++j) {
-      const uint64_t m = st->mpiv[j];  // only steps before j
+      const uint64_t m = __shfl_sync(0xffffffffu, j < 32 ? mlo : mhi, j & 31);  // only steps before j
       uint64_t acc = 0;
       if ((m >> lane) & 1u) acc ^= sE[lane];
       if ((m >> (lane + 32)) & 1u) acc ^= sE[lane + 32];
@@ -827,9 +841,16 @@ blk_rows_kernel(uint64_t *__restrict__ S, uint64_t nrows, const uint64_t *__rest
                 const int32_t *__restrict__ base, const int32_t *__restrict__ Tp, uint32_t chunks,
                 BlkState *st, uint64_t window_m0, uint64_t seed, uint64_t shot,
                 uint8_t *__restrict__ record, uint8_t *__restrict__ kinds, uint32_t *__restrict__ err) {
+  __shared__ int sw[64];          // 2 rV_s + A_s of each step
+  __shared__ uint64_t sG[64];     // G rows
   const int L = st->len;
   const uint64_t m0 = window_m0 + st->i0;  // record index of the block's first measurement
   const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((int)threadIdx.x < L) {  // blockDim >= 64 >= L
+    sw[threadIdx.x] = 2 * st->rV[threadIdx.x] + st->A[threadIdx.x];
+    sG[threadIdx.x] = st->G[threadIdx.x];
+  }
+  __syncthreads();
   if (r == 0) st->cursor = st->i0 + (uint32_t)L;  // the next block starts here
   if (r < (uint64_t)L) {
     const uint32_t b = (uint32_t)(philox4x64_10(m0 + r, shot, 0, 0, seed, kCoinKey).v[0] & 1u);
@@ -858,9 +879,9 @@ blk_rows_kernel(uint64_t *__restrict__ S, uint64_t nrows, const uint64_t *__rest
       while (mm) {
         const int s = __ffsll((long long)mm) - 1;
         mm &= mm - 1;
-        e += 2 * st->rV[s] + st->A[s];
+        e += sw[s];
       }
-      e += 2 * cross_pairs(st->G, sr);
+      e += 2 * cross_pairs(sG, sr);
       e = m4(e);
       if (e & 1) atomicOr(err, kErrOddPhase);
       nb = (uint64_t)(e >> 1);
