@@ -96,24 +96,13 @@ blk_init_kernel(const uint64_t *__restrict__ RX, uint32_t rs, uint64_t nrows, ui
   const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t c = 0;
   if (r < nrows) {
-    // eight steps' words loaded before any is used (independent loads in flight)
-    for (int j0 = 0; j0 < B; j0 += 8) {
-      uint32_t qq[8];
-      uint64_t wv[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        qq[t] = j0 + t < B ? qubits[j0 + t] : n;
-        wv[t] = qq[t] < n ? RX[r * rs + (qq[t] >> 6)] : 0;
-      }
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        if (j0 + t >= B) break;
-        if (qq[t] >= n) {
-          if (r == 0) atomicOr(err, kErrBadQubit);
-          continue;
-        }
-        c |= ((wv[t] >> (qq[t] & 63)) & 1ull) << (j0 + t);
-      }
+    uint32_t lastw = 0xFFFFFFFFu;
+    uint64_t word = 0;
+    for (int j = 0; j < B; ++j) {
+      const uint32_t q = qubits[j];
+      if (q >= n) { if (r == 0) atomicOr(err, kErrBadQubit); continue; }
+      if ((q >> 6) != lastw) { lastw = q >> 6; word = RX[r * rs + lastw]; }
+      c |= ((word >> (q & 63)) & 1ull) << j;
     }
     C[r] = c;
     M[r] = 0;
