@@ -361,18 +361,23 @@ blk_vrows_kernel(const uint64_t *__restrict__ RX, const uint64_t *__restrict__ R
     oz[j][lane] = in ? RZ[p * rs + u] : 0;
   }
   if (w == 0) {
-    // the steps' target masks, loaded once (lane l: steps l and l + 32) rather
-    // than one dependent global load per step of the loop below
+    // E_j = {j} + sum of E_s over the steps s < j that targeted p_j (m_j), one
+    // step after another: lane l keeps E_l and E_{l+32} in registers and each
+    // step is one XOR reduction over the warp; the masks are loaded once
     const uint64_t mlo = lane < L ? st->mpiv[lane] : 0, mhi = lane + 32 < L ? st->mpiv[lane + 32] : 0;
+    uint64_t elo = 0, ehi = 0;
     for (int j = 0; j < L; ++j) {
       const uint64_t m = __shfl_sync(0xffffffffu, j < 32 ? mlo : mhi, j & 31);  // only steps before j
-      uint64_t acc = 0;
-      if ((m >> lane) & 1u) acc ^= sE[lane];
-      if ((m >> (lane + 32)) & 1u) acc ^= sE[lane + 32];
-      for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) sE[j] = acc ^ (1ull << j);
-      __syncwarp();
+      const uint64_t acc = (((m >> lane) & 1u) ? elo : 0) ^ (((m >> (lane + 32)) & 1u) ? ehi : 0);
+      const uint64_t ej = (((uint64_t)__reduce_xor_sync(0xffffffffu, (uint32_t)(acc >> 32)) << 32) |
+                           __reduce_xor_sync(0xffffffffu, (uint32_t)acc)) ^ (1ull << j);
+      if (lane == (j & 31)) {
+        if (j < 32) elo = ej;
+        else ehi = ej;
+      }
     }
+    if (lane < L) sE[lane] = elo;
+    if (lane + 32 < L) sE[lane + 32] = ehi;
   }
   __syncthreads();
   // every block builds all V rows of its chunk (G needs them); the lead block
