@@ -708,6 +708,10 @@ __device__ __forceinline__ void apply_row(const ApplyRow &a, uint32_t nrows, uin
 // 1,024 threads at 64 registers: 6.80 ms per dense block at 180k, against
 // 7.46 ms with 768 threads (80 registers) and 9.55 ms with 512 (100)
 constexpr int kApplyThreads = 1024;
+// blocks per SM over the grid: 6.41 ms per dense 180k block with 32 waves of
+// one block per SM, 6.43 with 24, 6.49 with 16, 6.79 with 8, 7.46 with 4 (the
+// tails of the last wave shrink; a block's table build stays small)
+constexpr int kApplyWaves = 32;
 
 template <typename Idx>
 __global__ void __launch_bounds__(kApplyThreads, 1)
@@ -950,11 +954,11 @@ cudaError_t launch_measure_block(const Dev &d, void *scratch, const uint32_t *wi
   blk_signs_kernel<<<1, 64, 0, s>>>(d.S, st, d.err);
   blk_list_kernel<<<rb, 256, 0, s>>>(L.nrows, M, base, list, st);
   tend(d.timer, QS_TIME_BLK_PIVOT_ROWS, s);
-  // about 8 waves of one block per SM (the tables take 226 KB of shared
-  // memory and all of TMEM), but at least 512 rows per block so that building
-  // the tables stays small next to the rows they serve
+  // about kApplyWaves waves of one block per SM (the tables take 226 KB of
+  // shared memory and all of TMEM), but at least 512 rows per block so that
+  // building the tables stays small next to the rows they serve
   const uint32_t rows_y = std::max<uint32_t>(
-      1, (uint32_t)std::min<uint64_t>(((uint64_t)d.sms * 8 + chunks - 1) / chunks, L.nrows / 512));
+      1, (uint32_t)std::min<uint64_t>(((uint64_t)d.sms * kApplyWaves + chunks - 1) / chunks, L.nrows / 512));
   tbegin(d.timer, QS_TIME_BLK_APPLY, s);
   if (!d.wide_offsets && (uint64_t)L.nrows * L.rs < (1ull << 32))
     blk_apply_kernel<uint32_t><<<dim3(chunks, rows_y), kApplyThreads, smem, s>>>(
